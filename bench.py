@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the alternating-projection hot path on one or more GPUs.
+
+One step = one whole pass of the hot path on one synthetic problem: scale the
+inputs and build the FP64 block-Cholesky cache (ap_create), then run Alg. 1 to
+the tolerance with the fused residual update, Gauss-Southwell selection and the
+FP32 recompute that certifies the stopping rule (ap_solve).
+
+Workload (default): n = 262,144, d = 3, X ~ N(0, I), Matern-5/2 ARD with
+lengthscales log-uniform in [0.3, 3], noise 1e-2, blocks of 4096, B = [y, 15
+Rademacher probes], every column solved to ||r|| / ||b|| <= 1e-3.
+
+value = kernel-matrix entries evaluated per second over the whole step (the
+n*b entries of the cache plus n*b per AP step plus n^2 per FP32 recompute).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload and prints the same kind of line.
+Multi-GPU (torchrun): independent replicas, one problem per rank, no
+collective on the data path; value = all ranks' entries / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "AP time-to-tol & kernel-entries/s, BF16+refine vs FP32; serve p50/p99"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def workload(name: str, sub: int, n: int = 0):
+    kw = {"n": n} if n else {}
+    if name == "matern52_ard":
+        return wl.matern52_ard(sub=sub, **kw)
+    if name == "small_rbf":
+        return wl.small_rbf(sub=sub, **kw)
+    if name == "rbf_ard_large":
+        return wl.rbf_ard_large(sub=sub, **kw)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(p, args) -> dict:
+    return {"workload": f"{p.name}: {wl.KERNEL_NAMES[p.kernel]} ARD, n={p.n}, d={p.d}, b={p.block}, "
+                        f"c={p.c} (y + {p.c - 1} Rademacher probes), noise={p.noise:g}, "
+                        f"every column to ||r||/||b|| <= {p.tol:g}",
+            "n": p.n, "d": p.d, "block": p.block, "rhs": p.c, "tol": p.tol,
+            "kernel": wl.KERNEL_NAMES[p.kernel], "precision": args.precision, "stop": "max_rel",
+            "min_epochs": args.min_epochs, "max_epochs": args.max_epochs,
+            "l2": "inputs larger than L2 each step: the FP64 factor workspace and the FP32 "
+                  "inverse-factor cache are streamed through HBM",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ["kmv_fp32.cuh", "ap_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_2310_17137_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel: str, workload_name: str, n_launch_units: float):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    ent = t.get(f"{kernel}:{workload_name}")
+    if not ent or ent.get("src_hash") != kernel_src_hash():
+        return None
+    return ent["dram_bytes_per_launch"] * n_launch_units / ent.get("units_per_launch", n_launch_units)
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+
+    import paper_2310_17137_gb300 as ap
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = workload(args.workload, sub=rank, n=args.n)
+    prec = {"fp32": ap.AP_FP32, "bf16": ap.AP_BF16_REFINE, "fp16": ap.AP_FP16_REFINE}[args.precision]
+    hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+    X = torch.from_numpy(p.X).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    W = torch.empty_like(B)
+    stream = torch.cuda.current_stream(dev)
+
+    def opts():
+        return ap.ap_opts_default(block=p.block, tol=p.tol, stop=ap.AP_STOP_MAX_REL, min_epochs=args.min_epochs,
+                                  max_epochs=args.max_epochs, precision=prec, profile=1,
+                                  stream=stream.cuda_stream)
+
+    def one_step():
+        ctx = ap.ap_create(X, hyper, opts())
+        st, _, info, _ = ap.ap_solve(ctx, B, W=W)
+        launches = ap.ap_launch_count(ctx)
+        ap.ap_destroy(ctx)
+        return st, info, launches
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos, launches, statuses = [], 0, []
+    for _ in range(args.steps):
+        st, info, nl = one_step()
+        infos.append(info)
+        statuses.append(st)
+        launches += nl
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    cache_entries = float(p.n) * float(p.block)
+    entries = sum(cache_entries + i["kernel_entries"] for i in infos)
+    ent_t = torch.tensor([entries], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(ent_t)
+    total_entries = float(ent_t.item())
+    value = total_entries / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e_value = None
+    if not args.no_e2e:
+        e2e_value = end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist)
+    ttt = None
+    if rank == 0 and not args.no_ttt:
+        ttt = time_to_tol_small(ap, torch, dev, stream)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, infos[-1]["epochs"], args)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist):
+    Xh = torch.from_numpy(p.X).pin_memory()
+    Bh = torch.from_numpy(p.B).pin_memory()
+    Wh = torch.empty(p.B.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    e2e_entries = 0.0
+    cache_entries = float(p.n) * float(p.block)
+    for _ in range(args.steps):
+        Xd = Xh.to(dev, non_blocking=True)
+        Bd = Bh.to(dev, non_blocking=True)
+        ctx = ap.ap_create(Xd, hyper, opts())
+        st, Wd, info, _ = ap.ap_solve(ctx, Bd)
+        Wh.copy_(Wd, non_blocking=True)
+        ap.ap_destroy(ctx)
+        e2e_entries += cache_entries + info["kernel_entries"]
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    e2e_ms_t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
+        ent2 = torch.tensor([e2e_entries], device=dev, dtype=torch.float64)
+        dist.all_reduce(ent2)
+        e2e_entries = float(ent2.item())
+    return e2e_entries / (float(e2e_ms_t.item()) * 1e-3)
+
+
+def time_to_tol_small(ap, torch, dev, stream) -> dict:
+    """Time-to-tol of the plain FP32 solve on n = 4096 (RBF l = 0.5, noise 0.1,
+    blocks of 512, tol 1e-6, certified by the compensated FP32 recompute):
+    the configuration where AP reaches its tolerance within the epoch cap."""
+    p = wl.small_rbf()
+    X = torch.from_numpy(p.X).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+    times, infos = [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = ap.ap_create(X, hyper, ap.ap_opts_default(block=p.block, tol=p.tol, stop=ap.AP_STOP_MAX_REL,
+                                                        max_epochs=100000, stream=stream.cuda_stream))
+        st, W, info, _ = ap.ap_solve(ctx, B)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        infos.append(info)
+        ap.ap_destroy(ctx)
+    i = infos[-1]
+    return {"workload": "small_rbf n=4096 d=8 b=512 c=1 tol=1e-6 (FP32 form, compensated certification)",
+            "time_to_tol_s": statistics.median(times), "epochs": i["epochs"], "refinements": i["refinements"],
+            "rel_res_true": i["rel_res_true"][0], "status": ap.ap_status_str(st)}
+
+
+def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt) -> dict:
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    last = infos[-1]
+    n_up = max(1, last["n_update"])
+    t_launch = last["t_update_s"] / n_up
+    flops_per_entry = 2 * p.c + 3 * p.d
+    units = float(p.n) * float(p.block)
+    achieved = units * flops_per_entry / t_launch / 1e12 if t_launch > 0 else None
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = traffic_from_profiles("kmv_fp32_update", args.workload, units)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "kernel-entries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic (seeded NumPy PCG64; stands in for the paper's UCI sets)",
+        "config": describe(p, args),
+        "epochs": [i["epochs"] for i in infos],
+        "refinements": [i["refinements"] for i in infos],
+        "status": [ap.ap_status_str(s) for s in statuses],
+        "rel_res_max": max(max(i["rel_res_true"]) for i in infos),
+        "rel_res_y": infos[-1]["rel_res_true"][0],
+        "cache_s": statistics.median(i["t_cache_s"] for i in infos),
+        "solve_s": statistics.median(i["t_solve_s"] for i in infos),
+        "iteration_entries_per_s": statistics.median(i["entries_per_s"] for i in infos),
+        "update_kernel_ms": t_launch * 1e3,
+        "blocksolve_kernel_ms": last["t_blocksolve_s"] / n_up * 1e3,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "kmv_fp32_kernel (fused residual update, one AP step)",
+                     "flops_per_entry": flops_per_entry,
+                     "peak_note": f"FP32 FMA pipe: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                                  f"{sm_max:.0f} MHz (derived from unit counts and max clock)"},
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": "kernel-entries/s",
+            "h2d_bytes_per_step": int(p.X.nbytes + p.B.nbytes), "d2h_bytes_per_step": int(p.B.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "time_to_tol_small": ttt,
+    }
+    return line
+
+
+def cpu_baseline(p, epochs: int, args) -> dict:
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    same workload: one AP residual update over a row sample (the hot loop of
+    Alg. 1) and the Cholesky factorisation of one diagonal block; time-to-tol
+    is extrapolated to the whole step with the epoch count of the GPU run."""
+    import oracle
+    h = oracle.Hyper.of(p)
+    X = p.X.astype(np.float64)
+    rows = min(p.n, args.cpu_rows)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(p.n, rows, replace=False)).astype(np.int64)
+    b = p.block
+    delta = rng.standard_normal((b, p.c))
+    R = np.zeros((p.n, p.c))
+    t0 = time.perf_counter()
+    oracle.block_update(h, X, 0, delta, R, rows=idx)
+    t_upd = time.perf_counter() - t0
+    ent_per_s = rows * b / t_upd
+    Kii = oracle.gram(h, X[:b], X[:b], row0=0, col0=0)
+    t0 = time.perf_counter()
+    oracle.cholesky(Kii)
+    t_chol = time.perf_counter() - t0
+    m = -(-p.n // b)
+    steps = epochs * m
+    entries = float(p.n) * b + steps * float(p.n) * b + float(p.n) ** 2
+    t_total = m * t_chol + (steps * float(p.n) * b + float(p.n) ** 2) / ent_per_s
+    return {"value": entries / t_total, "unit": "kernel-entries/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"one residual update (Eq. text_update_of_r) over {rows} of {p.n} rows x b={b} "
+                      f"({t_upd:.1f} s) + FP64 Cholesky of one {b}x{b} block ({t_chol:.1f} s); "
+                      f"time-to-tol extrapolated to {m} blocks and {epochs} epochs = {t_total:.0f} s",
+            "time_to_tol_s_extrapolated": t_total}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    p = workload(args.workload, sub=0, n=args.n)
+    epochs = args.max_epochs
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(p, epochs, args))
+    t_all = time.perf_counter() - t_all
+    timed = vals[args.warmup:]
+    v = statistics.median(x["value"] for x in timed)
+    line = {
+        "metric": METRIC, "impl": "reference", "value": v, "unit": "kernel-entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.median(x["time_to_tol_s_extrapolated"] for x in timed) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded NumPy PCG64)", "config": describe(p, args),
+        "cpu_baseline": {"value": v, "unit": "kernel-entries/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": timed[-1]["sample"]},
+        "e2e": {"value": v, "unit": "kernel-entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": t_all,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap_ = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap_.add_argument("--gpus", type=int, default=1)
+    ap_.add_argument("--steps", type=int, default=3)
+    ap_.add_argument("--warmup", type=int, default=3)
+    ap_.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap_.add_argument("--workload", default="matern52_ard")
+    ap_.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap_.add_argument("--min-epochs", type=int, default=11)
+    ap_.add_argument("--max-epochs", type=int, default=30,
+                     help="epoch cap per solve (the configured tolerance is out of AP's reach on "
+                          "this workload within any practical cap; see the time_to_tol_small key)")
+    ap_.add_argument("--n", type=int, default=0, help="override n (profiling on a smaller case)")
+    ap_.add_argument("--cpu-rows", type=int, default=65536)
+    ap_.add_argument("--no-cpu-baseline", action="store_true")
+    ap_.add_argument("--no-e2e", action="store_true")
+    ap_.add_argument("--no-ttt", action="store_true")
+    args = ap_.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

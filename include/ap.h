@@ -1,0 +1,216 @@
+/*
+ * ap.h -- C ABI of the GB300 alternating-projection (AP) solver for Gaussian
+ * process kernel systems (K_hat) W = B, K_hat = s * k_l(X, X) + sigma^2 I.
+ *
+ * The method is Alg. 1 of Wu et al., "Large-Scale Gaussian Processes via
+ * Alternating Projection" (AISTATS 2024): per inner step select a block I by
+ * the modified Gauss-Southwell rule (Eq. approximate_gauss_southwell), solve
+ * Delta = K_II^{-1} R_I with the cached Cholesky factor of K_II (Sec. 3,
+ * "Cached Cholesky Factors"), then W_I += Delta (Eq. text_update_of_w) and
+ * R -= K_hat(X, X_I) Delta (Eq. text_update_of_r), the kernel block evaluated
+ * on the fly and never stored.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  X is n x d, B, W0, W, R are n x c, all FP32.
+ *     Pointers named *_dev are device pointers, *_host host pointers.
+ *   - The caller owns every buffer it passes.  X must stay alive and unchanged
+ *     for the life of the context (it is read again by ap_set_hyper).  The
+ *     context owns its scaled copy of X, the Cholesky cache and its work
+ *     buffers, and frees them in ap_destroy.
+ *   - Work is enqueued on opts.stream (a cudaStream_t, NULL = legacy stream),
+ *     and every call returns only once its results are in the caller's
+ *     buffers.
+ *   - Errors come back as ap_status codes; nothing exits, traps or prints.
+ *     After AP_ERR_CUDA the context should be destroyed.
+ *   - A context is not thread safe: one call at a time per context.
+ */
+#ifndef AP_H
+#define AP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AP_MAX_RHS 32 /* largest c (1 label column + up to 31 probes) */
+#define AP_MAX_DIM 32 /* largest input dimension d */
+
+typedef enum {
+    AP_OK = 0,
+    AP_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range */
+    AP_ERR_NOMEM = 2,         /* device allocation failed, or over opts.hbm_budget */
+    AP_ERR_NOT_SPD = 3,       /* a diagonal block K_II failed Cholesky: info.bad_block */
+    AP_ERR_NAN = 4,           /* a NaN or Inf appeared in the residual */
+    AP_ERR_NOT_CONVERGED = 5, /* max_epochs / max_steps reached; W and info still written */
+    AP_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (serving workers) */
+    AP_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    AP_ERR_UNSUPPORTED = 8    /* option combination not built */
+} ap_status;
+
+/* Kernel family, Sec. 5 ("Datasets and Models") and App. E (Matern nu = 1.5):
+ * k(x, x') = s * phi(r), r = ||(x - x') / l|| (ARD lengthscales l),
+ *   AP_RBF:      phi = exp(-r^2 / 2)
+ *   AP_MATERN32: phi = (1 + sqrt(3) r) exp(-sqrt(3) r)
+ *   AP_MATERN52: phi = (1 + sqrt(5) r + 5 r^2 / 3) exp(-sqrt(5) r)
+ * The noise sigma^2 is added on the index diagonal only (sigma^2 I). */
+typedef enum { AP_RBF = 0, AP_MATERN32 = 1, AP_MATERN52 = 2 } ap_kernel;
+
+/* Arithmetic of the residual update.
+ *   AP_FP32:         kernel blocks and contraction in FP32 (SIMT).
+ *   AP_BF16_REFINE:  kernel blocks and K*Delta on tensor cores with BF16
+ *                    operands and FP32 accumulation; accuracy recovered by
+ *                    recomputing R = B - K_hat W in the FP32 form (iterative
+ *                    refinement, justified by the residual lemma of App. B).
+ *   AP_FP16_REFINE:  as above with FP16 operands. */
+typedef enum { AP_FP32 = 0, AP_BF16_REFINE = 1, AP_FP16_REFINE = 2 } ap_precision;
+
+/* Block selection (Sec. 3, "Block Selection"): Gauss-Southwell on
+ * ||R_{I,:}||_F^2 (ties to the smallest block), cyclic (step j picks block
+ * j mod m), or uniform random (counter-based SplitMix64 of (seed, step)). */
+typedef enum { AP_SEL_GS = 0, AP_SEL_CYCLIC = 1, AP_SEL_RANDOM = 2 } ap_select;
+
+/* Stopping rule checked after every epoch (Sec. 5, "Alternating Projection
+ * Details"): MEAN_REL = average of per-column ||r_i|| / ||b_i|| strictly below
+ * tol (the paper's experiments); MAX_REL = every column <= tol; FRO =
+ * ||R||_F <= tol ||B||_F (Alg. 1); Y_REL = the first column only <= tol. */
+typedef enum { AP_STOP_MEAN_REL = 0, AP_STOP_MAX_REL = 1, AP_STOP_FRO = 2, AP_STOP_Y_REL = 3 } ap_stop;
+
+/* Arithmetic of the full residual recompute R = B - K_hat W (refinement and
+ * certification of the stopping rule, and ap_residual):
+ *   AP_RESID_AUTO:        compensated when opts.tol <= 1e-5, plain FP32 otherwise;
+ *   AP_RESID_FP32:        plain FP32 kernel entries and sums;
+ *   AP_RESID_COMPENSATED: double-float FP32 (error-free transformations), kernel
+ *                         entries to ~1e-11 relative; about 10x the cost. */
+typedef enum { AP_RESID_AUTO = 0, AP_RESID_FP32 = 1, AP_RESID_COMPENSATED = 2 } ap_residual_mode;
+
+/* Hyperparameters (Sec. 5): ARD lengthscales (host array of d floats),
+ * outputscale s, noise sigma^2 and constant prior mean mu. */
+typedef struct ap_hyper {
+    ap_kernel kernel;
+    int32_t d;
+    const float* lengthscale;
+    float outputscale;
+    float noise;
+    float mean;
+} ap_hyper;
+
+/* Solver options.  ap_opts_default fills the paper's values: GS selection,
+ * MEAN_REL with tol 1 (training), at least 11 and at most 1000 epochs. */
+typedef struct ap_opts {
+    int64_t block;        /* block size b (sequential partition, Sec. 5); last block may be short */
+    int32_t select;       /* ap_select */
+    int32_t stop;         /* ap_stop */
+    double tol;           /* stopping tolerance epsilon */
+    int32_t min_epochs;   /* default 11 */
+    int32_t max_epochs;   /* default 1000 */
+    int64_t max_steps;    /* > 0: stop after this many inner steps in total (bounded runs) */
+    int32_t precision;    /* ap_precision */
+    int32_t refine_every; /* low-precision forms: recompute R in FP32 every this many epochs */
+    uint64_t seed;        /* AP_SEL_RANDOM stream, and probes when ap_mll_grad gets Z_dev = NULL */
+    void* stream;         /* cudaStream_t for all work of this context */
+    size_t hbm_budget;    /* bytes the context may allocate; 0 = no limit */
+    int32_t* block_trace; /* optional host array: chosen block of each step */
+    int64_t trace_cap;    /* capacity of block_trace */
+    int32_t profile;      /* 1: time every block solve and residual update with CUDA events */
+    int32_t residual_mode; /* ap_residual_mode: arithmetic of the residual recompute */
+} ap_opts;
+
+/* Report of ap_solve / ap_mll_grad.  rel_res_* hold the first c columns. */
+typedef struct ap_info {
+    int32_t epochs;
+    int32_t refinements;
+    int64_t steps;
+    int32_t bad_block;                    /* AP_ERR_NOT_SPD: first failing block */
+    int32_t c;                            /* number of right-hand sides */
+    double rel_res_tracked[AP_MAX_RHS];   /* ||R_col|| / ||B_col|| of the tracked residual */
+    double rel_res_true[AP_MAX_RHS];      /* the same for B - K_hat W after the last refinement
+                                             (low-precision forms); equals tracked for FP32 */
+    double t_cache_s;                     /* Cholesky cache build time of the context */
+    double t_solve_s;                     /* wall time of the iteration */
+    double t_refine_s;                    /* part of t_solve_s spent in refinement passes */
+    double kernel_entries;                /* kernel-matrix entries evaluated by the iteration */
+    double entries_per_s;                 /* kernel_entries / t_solve_s */
+    int64_t gpu_launches;                 /* kernels launched by this call */
+    double data_fit;                      /* ap_mll_grad: 1/2 (y - mu)^T u, u = K_hat^{-1}(y - mu) */
+    double t_update_s;                    /* opts.profile: summed duration of the residual-update kernels */
+    int64_t n_update;                     /* opts.profile: number of residual-update launches timed */
+    double t_blocksolve_s;                /* opts.profile: summed duration of the block solves */
+} ap_info;
+
+typedef struct ap_ctx ap_ctx;
+
+/* Fill *o with the defaults: block 4096, GS, MEAN_REL, tol 1, 11..1000 epochs,
+ * FP32, refine_every 4, seed 0, default stream, no budget, no trace. */
+void ap_opts_default(ap_opts* o);
+
+/* Create a solver context for the n training inputs X_dev (device, n x d FP32,
+ * borrowed) and build the cached Cholesky factors of every diagonal block
+ * K_hat_II (Sec. 3, "Cached Cholesky Factors": factor once per hyperparameter
+ * setting; Table 6: (1/3) n b^2 flops, n b memory).  The factorisation runs in
+ * FP64; the factor's inverse L_I^{-1} is stored in FP32.
+ * Errors: INVALID_ARG (n < 1, d not in [1, 32], block < 1, bad hyper),
+ * NOMEM, NOT_SPD (no context is returned), CUDA. */
+ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d,
+                    const ap_hyper* h, const ap_opts* o);
+
+/* Replace the hyperparameters (same kernel family and d) and refactor the cache. */
+ap_status ap_set_hyper(ap_ctx* ctx, const ap_hyper* h);
+
+/* Solve K_hat W = B for c in [1, 32] right-hand sides by Alg. 1.  B_dev is
+ * n x c (device).  W0_dev (n x c, may be NULL) is a starting point: then R is
+ * first recomputed as B - K_hat W0 (warm start / resume).  W_dev (n x c) gets
+ * the result.  info (may be NULL) gets the report.
+ * Returns OK when the stopping rule held after >= min_epochs epochs,
+ * NOT_CONVERGED at max_epochs / max_steps (W still written), NAN, CUDA. */
+ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_dev,
+                   float* W_dev, ap_info* info);
+
+/* True residual R = B - K_hat W (n x c, device), FP32 form, all n^2 kernel
+ * entries evaluated on the fly (the residual lemma of App. B).  Used for
+ * refinement and certification. */
+ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W_dev,
+                      float* R_dev);
+
+/* Posterior mean (Sec. 2): mean_dev[t] = mu + s * sum_j phi(x*_t, x_j) w_j for
+ * the M test inputs Xs_dev (device, M x d).  w_dev (device, n) is
+ * K_hat^{-1} (y - mu), e.g. column 0 of ap_solve's W.  No noise term. */
+ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, int64_t M,
+                          float* mean_dev);
+
+/* The fused derivative quadratic forms of Eq. loss_grad_unbiased:
+ *   out_host[p] = sum_col alpha_host[col] * U[:,col]^T (dK_hat / dtheta_p) V[:,col]
+ * for theta = (l_1..l_d, s, sigma^2): d + 2 doubles.  U_dev, V_dev are n x c
+ * (device), alpha_host has c entries.  One pass over all n^2 kernel entries;
+ * no kernel block is stored. */
+ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c,
+                            const double* alpha_host, double* out_host);
+
+/* Stochastic gradient of the negative MLL (Eq. loss_grad_unbiased): solves
+ * K_hat [u, w_1..w_l] = [y - mu, z_1..z_l] with AP, then
+ *   g_theta = -1/2 u^T K' u + 1/(2l) sum_i w_i^T K' z_i,  g_mu = -1^T u.
+ * y_dev (device, n); Z_dev (device, n x l Rademacher probes) or NULL to draw
+ * them from SplitMix64(opts.seed); n_probes = l in [0, 31].
+ * grad_host gets d + 3 floats: l_1..l_d, s, sigma^2, mu.  Status as ap_solve. */
+ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const float* Z_dev,
+                      float* grad_host, ap_info* info);
+
+/* Number of kernels this context has launched since ap_create (all calls). */
+int64_t ap_launch_count(const ap_ctx* ctx);
+
+/* Release everything the context owns.  NULL is allowed. */
+void ap_destroy(ap_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* ap_status_str(ap_status s);
+
+/* Size in bytes of the structs above, for bindings that mirror them. */
+size_t ap_sizeof_opts(void);
+size_t ap_sizeof_info(void);
+size_t ap_sizeof_hyper(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AP_H */

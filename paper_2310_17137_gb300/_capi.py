@@ -1,0 +1,95 @@
+"""ctypes mirror of include/ap.h.  Argument marshalling only: every step of the
+solver runs in libap.so's CUDA kernels; nothing here computes."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+AP_MAX_RHS = 32
+AP_MAX_DIM = 32
+
+AP_OK, AP_ERR_INVALID_ARG, AP_ERR_NOMEM, AP_ERR_NOT_SPD, AP_ERR_NAN = 0, 1, 2, 3, 4
+AP_ERR_NOT_CONVERGED, AP_ERR_TIMEOUT, AP_ERR_CUDA, AP_ERR_UNSUPPORTED = 5, 6, 7, 8
+AP_RBF, AP_MATERN32, AP_MATERN52 = 0, 1, 2
+AP_FP32, AP_BF16_REFINE, AP_FP16_REFINE = 0, 1, 2
+AP_SEL_GS, AP_SEL_CYCLIC, AP_SEL_RANDOM = 0, 1, 2
+AP_STOP_MEAN_REL, AP_STOP_MAX_REL, AP_STOP_FRO, AP_STOP_Y_REL = 0, 1, 2, 3
+AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED = 0, 1, 2
+
+# every function include/ap.h declares
+EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_residual",
+           "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy", "ap_status_str",
+           "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count"]
+
+
+class ap_hyper(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("d", ctypes.c_int32), ("lengthscale", ctypes.c_void_p),
+                ("outputscale", ctypes.c_float), ("noise", ctypes.c_float), ("mean", ctypes.c_float)]
+
+
+class ap_opts(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int64), ("select", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("min_epochs", ctypes.c_int32), ("max_epochs", ctypes.c_int32),
+                ("max_steps", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("refine_every", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("hbm_budget", ctypes.c_size_t), ("block_trace", ctypes.POINTER(ctypes.c_int32)),
+                ("trace_cap", ctypes.c_int64), ("profile", ctypes.c_int32),
+                ("residual_mode", ctypes.c_int32)]
+
+
+class ap_info(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("refinements", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("bad_block", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("rel_res_tracked", ctypes.c_double * AP_MAX_RHS),
+                ("rel_res_true", ctypes.c_double * AP_MAX_RHS),
+                ("t_cache_s", ctypes.c_double), ("t_solve_s", ctypes.c_double),
+                ("t_refine_s", ctypes.c_double), ("kernel_entries", ctypes.c_double),
+                ("entries_per_s", ctypes.c_double), ("gpu_launches", ctypes.c_int64),
+                ("data_fit", ctypes.c_double), ("t_update_s", ctypes.c_double),
+                ("n_update", ctypes.c_int64), ("t_blocksolve_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libap.so (building it first if it is missing).  There is no fallback:
+    if the CUDA library cannot be built or loaded this raises."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError(f"{_build.LIB} is missing; run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    st = ctypes.c_int
+    sig = {
+        "ap_opts_default": (None, [ctypes.POINTER(ap_opts)]),
+        "ap_create": (st, [ctypes.POINTER(P), P, i64, i32, ctypes.POINTER(ap_hyper), ctypes.POINTER(ap_opts)]),
+        "ap_set_hyper": (st, [P, ctypes.POINTER(ap_hyper)]),
+        "ap_solve": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
+        "ap_residual": (st, [P, P, i32, P, P]),
+        "ap_predict_mean": (st, [P, P, P, i64, P]),
+        "ap_grad_quadforms": (st, [P, P, P, i32, P, P]),
+        "ap_mll_grad": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
+        "ap_destroy": (None, [P]),
+        "ap_launch_count": (i64, [P]),
+        "ap_status_str": (ctypes.c_char_p, [st]),
+        "ap_sizeof_opts": (ctypes.c_size_t, []),
+        "ap_sizeof_info": (ctypes.c_size_t, []),
+        "ap_sizeof_hyper": (ctypes.c_size_t, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L

@@ -1,0 +1,168 @@
+// Internal declarations shared by the CUDA translation units of libap.so.
+// Nothing here is part of the public ABI (include/ap.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ap.h"
+
+namespace ap {
+
+constexpr int kTile = 64;           // tile edge of the block-Cholesky cache
+constexpr int kKmvThreads = 128;    // threads per CTA of the kernel-matrix products
+constexpr int kKmvTN = 64;          // columns staged per shared-memory chunk
+constexpr int kMaxSplit = 8;        // portable thread-block-cluster size
+
+// flags of the kernel-matrix product epilogue
+constexpr int kEpiBlockNorms = 1;   // per-block ||R_J||_F^2 partials + block selection
+constexpr int kEpiColNorms = 2;     // per-column ||R_:,c||^2 partials
+
+// Scale applied to x / l so that the FP32 kernels evaluate phi with one ex2:
+//   RBF:  |x_s - x_s'|^2 = r^2 log2(e) / 2          -> phi = 2^(-|.|^2)
+//   M32:  |x_s - x_s'|   = sqrt(3) r = u             -> phi = (1 + u) 2^(-u log2 e)
+//   M52:  |x_s - x_s'|   = sqrt(5) r = u             -> phi = (1 + u + u^2/3) 2^(-u log2 e)
+double kernel_input_scale(int kernel);
+
+// Epilogue bookkeeping of one AP step (block norms, selection, column norms).
+struct EpiParams {
+    int flags;
+    int advance;            // 1: a step finished (step_ctr += 1) before selecting
+    int64_t seg;            // rows per AP block b (tiles never straddle a block)
+    int64_t tiles_per_seg;  // CTA row tiles per block
+    int64_t ntiles;         // row tiles in the grid (y dimension)
+    int S;                  // CTAs per row tile (cluster size, x dimension)
+    int m;                  // number of blocks
+    double* part_norm;      // [ntiles * S]
+    double* part_col;       // [ntiles * S * C]
+    unsigned int* ticket;   // last-CTA counter, left at 0 after each launch
+    double* norms_out;      // [m]   block norms after the step
+    double* colnorm_out;    // [C]   column norms (when kEpiColNorms)
+    int select;             // ap_select
+    uint64_t seed;
+    int64_t* step_ctr;      // steps completed (device)
+    int* sel_out;           // block chosen for the next step (device)
+    int* nan_flag;          // set to 1 when a norm is not finite
+};
+
+// out[i,:] = base[i,:] + sgn * s * sum_j phi(xa_i, xb_j) V[j - col0, :]
+//            + sgn * noise * V[i - col0, :]   (if noise_diag and col0 <= i < col0 + ncols)
+struct KmvParams {
+    const float* Xa;       // na x D scaled rows
+    int64_t na;
+    const float* Xb;       // nb x D scaled columns
+    int64_t nb;
+    const float* V;        // ncols x C
+    const float* base;     // na x C or nullptr (then base_const)
+    float base_const;
+    float* out;            // na x C (may alias base)
+    float sgn;
+    float s;
+    float noise;
+    int noise_diag;
+    int64_t col0, ncols;   // column range when sel == nullptr
+    const int* sel;        // device block index: col0 = sel*blk, ncols = min(blk, nb - col0)
+    int64_t blk;
+    const float* Xa_lo;    // compensated form only: low parts of the scaled inputs
+    const float* Xb_lo;
+    EpiParams epi;
+};
+
+// FP32 SIMT kernel-matrix product with the AP epilogue (one per kernel family TU).
+cudaError_t launch_kmv_rbf(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv_m32(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv_m52(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv(int kernel, const KmvParams& p, int D, int C, cudaStream_t st);
+// Compensated (double-float FP32) form of the same product, for refinement.
+cudaError_t launch_kmv_comp_rbf(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv_comp_m32(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv_comp_m52(const KmvParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_kmv_comp(int kernel, const KmvParams& p, int D, int C, cudaStream_t st);
+constexpr int kCompRows = 128;  // rows per CTA of the compensated product
+
+// Rows per CTA for a (D, C) instance of the FP32 product.
+int kmv_rows_per_cta(int D, int C);
+
+// Norms of R alone (n x C) + selection: used before the first step and after refinement.
+cudaError_t launch_norms_select(const float* R, int64_t n, int C, const EpiParams& e,
+                                int64_t tile_rows, cudaStream_t st);
+
+// ---- block-Cholesky cache (FP64 factorisation, FP32 inverse factor) --------
+struct CacheParams {
+    const float* X;        // n x d, original inputs
+    int64_t n;
+    int d;
+    int kernel;
+    double ell[AP_MAX_DIM];
+    double s, noise;
+    int64_t b;             // block size
+    int nt;                // tiles per block edge = ceil(b / kTile)
+};
+
+// Factor blocks [blk0, blk0 + g) into the packed FP32 inverse factors Linv.
+// A (g * (nt*64)^2 doubles) and Dinv (g * nt * 64^2 doubles) are work buffers.
+// bad (g ints) gets 1 for a block whose factorisation met a non-positive pivot.
+cudaError_t cache_factor_group(const CacheParams& cp, int64_t blk0, int g, double* A, double* Dinv,
+                               float* Linv, int* bad, cudaStream_t st, int64_t* launches);
+
+// ---- block solve: Delta = L^-T L^-1 R_I, W_I += Delta -----------------------
+struct SolveParams {
+    const float* Linv;     // packed inverse factors of all blocks
+    int64_t n, b;
+    int nt;
+    int C;
+    const float* R;        // n x C
+    float* W;              // n x C
+    float* Z;              // nt*64 x C work
+    float* Delta;          // b x C (rows >= b_I are written as 0)
+    const int* sel;
+    const int64_t* step_ctr;
+    int* trace;            // device trace or nullptr
+    int64_t trace_cap;
+};
+cudaError_t launch_block_solve(const SolveParams& p, cudaStream_t st, int64_t* launches);
+
+// ---- small helpers ----------------------------------------------------------
+// Xs = fl(X * sc) with sc = sc_hi + sc_lo per dimension; Xs_lo (may be null)
+// gets the remainder X * sc - Xs to FP32 precision.
+cudaError_t launch_prep_inputs(const float* X, int64_t n, int d, int D, const float* sc_hi, const float* sc_lo,
+                               float* Xs, float* Xs_lo, cudaStream_t st);
+cudaError_t launch_pad_copy(const float* src, int64_t n, int c, float* dst, int C, cudaStream_t st);
+cudaError_t launch_unpad_copy(const float* src, int64_t n, int C, float* dst, int c, cudaStream_t st);
+
+// ---- derivative quadratic forms (Eq. loss_grad_unbiased) ------------------
+// Accumulates, over all pairs (i, j), G_ij = sum_c alpha_c U_ic V_jc times
+//   out[k]     (k < D): G_ij psi(t_ij) (xs_ik - xs_jk)^2   (lengthscale terms)
+//   out[D]:            G_ij phi(t_ij)                      (outputscale term)
+//   out[D + 1]:        G_ii                                 (noise term)
+// with the pre-scaled inputs xs of the FP32 product; the host turns these
+// into dK/dtheta quadratic forms.
+struct GradParams {
+    const float* Xs;       // n x D scaled inputs
+    int64_t n;
+    const float* U;        // n x C
+    const float* V;        // n x C
+    float alpha[AP_MAX_RHS];
+    int64_t ntiles;        // row tiles (grid.x)
+    int S;                 // column splits (grid.y)
+    double* part;          // [ntiles * S * (D + 2)]
+    unsigned int* ticket;
+    double* out;           // D + 2
+};
+cudaError_t launch_grad(int kernel, const GradParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_grad_rbf(const GradParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_grad_m32(const GradParams& p, int D, int C, cudaStream_t st);
+cudaError_t launch_grad_m52(const GradParams& p, int D, int C, cudaStream_t st);
+int grad_rows_per_cta(int D, int C);
+
+// B = [y - mu, z_1..z_l]; Z == nullptr draws Rademacher z from SplitMix64(seed);
+// Zout (may be nullptr) receives the z actually used.
+cudaError_t launch_assemble_rhs(const float* y, float mu, const float* Z, int l, uint64_t seed, int64_t n,
+                                float* B, float* Zout, cudaStream_t st);
+// V = [W[:,0], B[:,1..c)] padded to C columns.
+cudaError_t launch_assemble_v(const float* W, int C, const float* B, int c, int64_t n, float* V, cudaStream_t st);
+// out = sum_i W[i*C] * (Y ? Y[i*cy] : 1) in FP64; part needs 256 doubles.
+cudaError_t launch_dot0(const float* W, int C, const float* Y, int cy, int64_t n, double* part, unsigned* ticket,
+                       double* out, cudaStream_t st);
+
+}  // namespace ap

@@ -1,0 +1,8 @@
+// Fused MLL-gradient backward instances for one kernel family (see grad.cuh).
+#include "grad.cuh"
+
+namespace ap {
+cudaError_t launch_grad_rbf(const GradParams& p, int D, int C, cudaStream_t st) {
+    return dispatch_grad<AP_RBF>(p, D, C, st);
+}
+}  // namespace ap

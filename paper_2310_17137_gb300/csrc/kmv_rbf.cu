@@ -1,0 +1,8 @@
+// FP32 kernel-matrix product instances for one kernel family (see kmv_fp32.cuh).
+#include "kmv_fp32.cuh"
+
+namespace ap {
+cudaError_t launch_kmv_rbf(const KmvParams& p, int D, int C, cudaStream_t st) {
+    return dispatch_kmv<AP_RBF>(p, D, C, st);
+}
+}  // namespace ap
