@@ -46,7 +46,8 @@ typedef enum {
     AP_ERR_NOT_CONVERGED = 5, /* max_epochs / max_steps reached; W and info still written */
     AP_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (serving workers) */
     AP_ERR_CUDA = 7,          /* a CUDA runtime call failed */
-    AP_ERR_UNSUPPORTED = 8    /* option combination not built */
+    AP_ERR_UNSUPPORTED = 8,   /* option combination not built */
+    AP_ERR_SCRATCH_LIMIT = 9  /* ap_grad_quadforms_static: problem exceeds the fixed scratch */
 } ap_status;
 
 /* Kernel family, Sec. 5 ("Datasets and Models") and App. E (Matern nu = 1.5):
@@ -186,6 +187,36 @@ ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, 
  * no kernel block is stored. */
 ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c,
                             const double* alpha_host, double* out_host);
+
+/* Size of the fixed device scratch array compiled into libap.so for
+ * ap_grad_quadforms_static (per GPU that loads the library, held until exit). */
+#define AP_STATIC_SCRATCH_BYTES (1u << 20)
+
+/* ap_grad_quadforms without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate in
+ * their steady state -- code running while a CUDA stream is being captured
+ * into a graph, latency-bound serving loops (cudaMalloc and cudaFree
+ * synchronise the whole device), and processes whose memory pool already owns
+ * the free HBM.  Such a caller creates the context once at set-up (ap_create
+ * allocates) and then calls this function, which calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
+ *   - Same result as ap_grad_quadforms (same kernel; only the order in which
+ *     the per-CTA partial sums are added may differ).
+ *   - c must be 1, 4, 16 or 32: U_dev and V_dev (n x c, device) are read in
+ *     place, without a padding copy.
+ *   - Scratch: one AP_STATIC_SCRATCH_BYTES device array shared by every call
+ *     in the process, holding (D + 2) doubles per block of 128 rows (256 rows
+ *     when D + c <= 40), D = d rounded up to 4, 8, 12, 16, 24 or 32: n up to
+ *     about 490k at d = 32 with c = 32 and 3.3M at d <= 8.  A larger problem
+ *     returns AP_ERR_SCRATCH_LIMIT before anything is launched.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Work runs on the context's stream (opts.stream) and the call returns
+ *     when out_host is written.  Calls that overlap on the GPU (from several
+ *     threads or streams) share the scratch and race: serialise them. */
+ap_status ap_grad_quadforms_static(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c,
+                                   const double* alpha_host, double* out_host);
 
 /* Stochastic gradient of the negative MLL (Eq. loss_grad_unbiased): solves
  * K_hat [u, w_1..w_l] = [y - mu, z_1..z_l] with AP, then

@@ -19,7 +19,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _capi
-from ._capi import (AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_INVALID_ARG, AP_ERR_NAN, AP_ERR_NOMEM,  # noqa: F401
+from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_INVALID_ARG, AP_ERR_NAN, AP_ERR_NOMEM,  # noqa: F401
                     AP_ERR_NOT_CONVERGED, AP_ERR_NOT_SPD, AP_ERR_TIMEOUT, AP_ERR_UNSUPPORTED,
                     AP_FP16_REFINE, AP_FP32, AP_MATERN32, AP_MATERN52, AP_OK, AP_RBF, AP_SEL_CYCLIC,
                     AP_SEL_GS, AP_SEL_RANDOM, AP_STOP_FRO, AP_STOP_MAX_REL, AP_STOP_MEAN_REL,
@@ -27,7 +27,7 @@ from ._capi import (AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_INVALID_ARG, AP_ERR_NAN,
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "MLLDataFit"]
+           "ap_status_str", "ap_launch_count", "ap_grad_quadforms_static", "MLLDataFit"]
 
 
 class ApError(RuntimeError):
@@ -186,6 +186,21 @@ def ap_grad_quadforms(ctx: Context, U, V, alpha) -> np.ndarray:
                                         out.ctypes.data)
     if st != AP_OK:
         raise ApError(st, "ap_grad_quadforms")
+    return out
+
+
+def ap_grad_quadforms_static(ctx: Context, U, V, alpha) -> np.ndarray:
+    """ap_grad_quadforms without device allocation (fixed scratch inside libap.so);
+    for callers that may not allocate in their steady state.  c must be 1, 4,
+    16 or 32; overlapping calls share the scratch and must be serialised."""
+    U2 = U if U.dim() == 2 else U.reshape(-1, 1)
+    V2 = V if V.dim() == 2 else V.reshape(-1, 1)
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+    out = np.zeros(ctx.d + 2)
+    st = _capi.load().ap_grad_quadforms_static(ctx.handle, _ptr(U2), _ptr(V2), U2.shape[1], a.ctypes.data,
+                                               out.ctypes.data)
+    if st != AP_OK:
+        raise ApError(st, "ap_grad_quadforms_static")
     return out
 
 

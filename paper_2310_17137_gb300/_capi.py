@@ -12,6 +12,8 @@ AP_MAX_DIM = 32
 
 AP_OK, AP_ERR_INVALID_ARG, AP_ERR_NOMEM, AP_ERR_NOT_SPD, AP_ERR_NAN = 0, 1, 2, 3, 4
 AP_ERR_NOT_CONVERGED, AP_ERR_TIMEOUT, AP_ERR_CUDA, AP_ERR_UNSUPPORTED = 5, 6, 7, 8
+AP_ERR_SCRATCH_LIMIT = 9
+AP_STATIC_SCRATCH_BYTES = 1 << 20
 AP_RBF, AP_MATERN32, AP_MATERN52 = 0, 1, 2
 AP_FP32, AP_BF16_REFINE, AP_FP16_REFINE = 0, 1, 2
 AP_SEL_GS, AP_SEL_CYCLIC, AP_SEL_RANDOM = 0, 1, 2
@@ -21,7 +23,8 @@ AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED = 0, 1, 2
 # every function include/ap.h declares
 EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_residual",
            "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy", "ap_status_str",
-           "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count"]
+           "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count",
+           "ap_grad_quadforms_static"]
 
 
 class ap_hyper(ctypes.Structure):
@@ -79,6 +82,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_residual": (st, [P, P, i32, P, P]),
         "ap_predict_mean": (st, [P, P, P, i64, P]),
         "ap_grad_quadforms": (st, [P, P, P, i32, P, P]),
+        "ap_grad_quadforms_static": (st, [P, P, P, i32, P, P]),
         "ap_mll_grad": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
         "ap_destroy": (None, [P]),
         "ap_launch_count": (i64, [P]),

@@ -636,6 +636,28 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
 
 }  // namespace
 
+namespace ap {
+
+void ctx_grad_view(const ap_ctx* ctx, GradView* v) {
+    v->Xs = ctx->Xs;
+    v->n = ctx->n;
+    v->d = ctx->d;
+    v->D = ctx->D;
+    v->kernel = ctx->kernel;
+    v->s = ctx->s;
+    v->ell = ctx->ell;
+    v->stream = ctx->ust;
+}
+
+void grad_finish(const GradView& v, const double* raw, double* out_host) {
+    const double fac = v.kernel == AP_RBF ? 2.0 / 1.4426950408889634 : (v.kernel == AP_MATERN32 ? 1.0 : 1.0 / 3.0);
+    for (int k = 0; k < v.d; ++k) out_host[k] = (double)v.s * fac * raw[k] / (double)v.ell[k];
+    out_host[v.d] = raw[v.D];
+    out_host[v.d + 1] = raw[v.D + 1];
+}
+
+}  // namespace ap
+
 extern "C" {
 
 void ap_opts_default(ap_opts* o) {
@@ -674,6 +696,7 @@ const char* ap_status_str(ap_status s) {
         case AP_ERR_TIMEOUT: return "AP_ERR_TIMEOUT";
         case AP_ERR_CUDA: return "AP_ERR_CUDA";
         case AP_ERR_UNSUPPORTED: return "AP_ERR_UNSUPPORTED";
+        case AP_ERR_SCRATCH_LIMIT: return "AP_ERR_SCRATCH_LIMIT";
     }
     return "AP_ERR_UNKNOWN";
 }

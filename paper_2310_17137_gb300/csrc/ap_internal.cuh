@@ -165,4 +165,17 @@ cudaError_t launch_assemble_v(const float* W, int C, const float* B, int c, int6
 cudaError_t launch_dot0(const float* W, int C, const float* Y, int cy, int64_t n, double* part, unsigned* ticket,
                        double* out, cudaStream_t st);
 
+// Read-only view of what the gradient kernel needs from a context.
+struct GradView {
+    const float* Xs;
+    int64_t n;
+    int d, D, kernel;
+    float s;
+    const float* ell;
+    cudaStream_t stream;  // the caller's stream of the context
+};
+void ctx_grad_view(const ap_ctx* ctx, GradView* v);
+// Turn the raw D + 2 sums of the gradient kernel into the d + 2 quadratic forms.
+void grad_finish(const GradView& v, const double* raw, double* out_host);
+
 }  // namespace ap
