@@ -297,11 +297,8 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
     last = infos[-1]
     n_up = max(1, last["n_update"])
     t_launch = last["t_update_s"] / n_up
-    flops_per_entry = 2 * p.c + 3 * p.d
     units = float(p.n) * float(p.block)
-    achieved = units * flops_per_entry / t_launch / 1e12 if t_launch > 0 else None
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    traffic = traffic_from_profiles("kmv_fp32_update", args.workload, units)
+    roof = roofline(p, args, t_launch, units, sm_max)
     line = {
         "metric": METRIC,
         "value": value,
@@ -326,12 +323,7 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "iteration_entries_per_s": statistics.median(i["entries_per_s"] for i in infos),
         "update_kernel_ms": t_launch * 1e3,
         "blocksolve_kernel_ms": last["t_blocksolve_s"] / n_up * 1e3,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "kmv_fp32_kernel (fused residual update, one AP step)",
-                     "flops_per_entry": flops_per_entry,
-                     "peak_note": f"FP32 FMA pipe: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                                  f"{sm_max:.0f} MHz (derived from unit counts and max clock)"},
+        "roofline": roof,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": "kernel-entries/s",
             "h2d_bytes_per_step": int(p.X.nbytes + p.B.nbytes), "d2h_bytes_per_step": int(p.B.nbytes)},
@@ -340,6 +332,42 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "time_to_tol_small": ttt,
     }
     return line
+
+
+# MUFU results per clock per SM on GB300.  ncu's pct-of-peak for the XU pipe
+# (28 % at 7.75 results/clk/SM measured on the tensor-core update kernel) puts
+# the pipe's peak at ~32/clk/SM (Blackwell Ultra doubled the SFU rate).
+SFU_OPS_PER_SM = 32
+
+
+def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
+    """Roofline of the dominant kernel (the fused residual update of one AP step)."""
+    if args.precision == "fp32":
+        flops_per_entry = 2 * p.c + 3 * p.d
+        achieved = units * flops_per_entry / t_launch / 1e12 if t_launch > 0 else None
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic_from_profiles("kmv_fp32_update", args.workload, units),
+                "kernel": "kmv_fp32_kernel (fused residual update, one AP step)",
+                "per_unit": f"{flops_per_entry} FP32 flop per kernel entry (2c contraction + 3d distance)",
+                "peak_note": f"FP32 FMA pipe: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                             f"{sm_max:.0f} MHz (derived from unit counts and max clock)"}
+    mufu = 1 if p.kernel == wl.RBF else 2
+    achieved = units * mufu / t_launch / 1e12 if t_launch > 0 else None
+    peak = NUM_SMS * SFU_OPS_PER_SM * sm_max * 1e6 / 1e12
+    kd = 16 if p.d + 2 <= 16 else 32
+    cp = max(16, p.c)
+    tensor_flops = 3 * 2 * kd + 3 * 2 * cp
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_from_profiles("kmv_tc_update", args.workload, units),
+            "kernel": "kmv_tc_kernel (tcgen05 fused residual update, one AP step)",
+            "per_unit": f"{mufu} SFU (MUFU) op per kernel entry; units are tera-ops/s of the SFU pipe",
+            "peak_note": f"SFU pipe: {NUM_SMS} SMs x {SFU_OPS_PER_SM} results/clk x {sm_max:.0f} MHz "
+                         "(derived from unit counts and max clock)",
+            "tensor_tflops": units * tensor_flops / t_launch / 1e12 if t_launch > 0 else None,
+            "tensor_flops_per_entry": tensor_flops}
 
 
 def cpu_baseline(p, epochs: int, args) -> dict:

@@ -61,6 +61,12 @@ struct ap_ctx {
     double t_update = 0.0, t_bsolve = 0.0;
     int64_t n_update = 0;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
+    // tensor-core form (AP_BF16_REFINE)
+    bool tc = false;
+    int kd = 16, cpb = 0, num_sms = 152;
+    int64_t tps128 = 0;
+    uint8_t *XA = nullptr, *XB = nullptr, *DT = nullptr;
+    int* tc_err = nullptr;
     int64_t launches = 0;
     cudaError_t last_cuda = cudaSuccess;
 };
@@ -228,6 +234,11 @@ bool use_compensated(const ap_ctx* ctx) {
 ap_status build_cache(ap_ctx* ctx) {
     drop_graph(ctx);
     AP_TRY(prep_inputs(ctx, ctx->X, ctx->n, ctx->Xs, ctx->Xs_lo));
+    if (ctx->tc) {
+        AP_CK(launch_tc_pack_inputs(ctx->kernel, ctx->Xs, ctx->n, ctx->d, ctx->D, ctx->b, ctx->m, ctx->tps128, ctx->cpb, ctx->kd,
+                                    ctx->XA, ctx->XB, ctx->st));
+        ctx->launches += 2;
+    }
     const int64_t tile_elems = (int64_t)kTile * kTile;
     if (!ctx->Linv) AP_TRY(dalloc_t(ctx, &ctx->Linv, (size_t)(ctx->m * ctx->ntri * tile_elems)));
     const int64_t edge = (int64_t)ctx->nt * kTile;
@@ -313,6 +324,11 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         const Shape a = step_shape(ctx, Cp, ctx->b), b = step_shape(ctx, Cp, ctx->n), c = norm_shape(ctx);
         const Shape d = comp_shape(ctx, ctx->n);
         int64_t need = std::max(std::max(a.ntiles * a.S, b.ntiles * b.S), std::max(c.ntiles, d.ntiles * d.S));
+        need = std::max(need, ctx->m * ctx->tps128);
+        if (ctx->tc) {
+            dfree(ctx, ctx->DT);
+            AP_TRY(dalloc_t(ctx, &ctx->DT, tc_delta_bytes(ctx->cpb, Cp)));
+        }
         dfree(ctx, ctx->part_norm);
         AP_TRY(dalloc_t(ctx, &ctx->part_norm, (size_t)need));
         AP_TRY(dalloc_t(ctx, &ctx->part_col, (size_t)need * Cp));
@@ -343,9 +359,39 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
     sp.trace = ctx->trace;
     sp.trace_cap = ctx->trace_alloc;
     AP_CK(launch_block_solve(sp, ctx->st, &ctx->launches));
+    if (ctx->tc) {
+        AP_CK(launch_tc_pack_delta(ctx->Delta, ctx->b, Cp, ctx->cpb, ctx->DT, ctx->st));
+        ++ctx->launches;
+    }
     if (prof) {
         AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j + 1], ctx->st, cudaEventRecordExternal));
         AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j], ctx->st, cudaEventRecordExternal));
+    }
+    if (ctx->tc) {
+        Shape sh;
+        sh.rows = 128;
+        sh.tps = ctx->tps128;
+        sh.ntiles = ctx->m * ctx->tps128;
+        sh.S = 1;
+        TcLaunch tl = {};
+        tl.XA = ctx->XA;
+        tl.XB = ctx->XB;
+        tl.DT = ctx->DT;
+        tl.Delta = ctx->Delta;
+        tl.R = ctx->R;
+        tl.n = ctx->n;
+        tl.b = ctx->b;
+        tl.cpb = ctx->cpb;
+        tl.s = ctx->s;
+        tl.noise = ctx->noise;
+        tl.sel = ctx->sel;
+        tl.err = ctx->tc_err;
+        tl.epi = make_epi(ctx, kEpiBlockNorms | (colnorms ? kEpiColNorms : 0), 1, sh);
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, sh.ntiles);
+        AP_CK(launch_kmv_tc_step(ctx->kernel, tl, ctx->kd, Cp, grid, ctx->st));
+        ++ctx->launches;
+        if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j + 1], ctx->st, cudaEventRecordExternal));
+        return AP_OK;
     }
     const Shape sh = step_shape(ctx, Cp, ctx->b);
     KmvParams kp = {};
@@ -440,7 +486,7 @@ ap_status run_epoch(ap_ctx* ctx, int64_t steps) {
         }
         if (ctx->graph) {
             AP_CK(cudaGraphLaunch(ctx->graph, ctx->st));
-            ctx->launches += 3 * steps;
+            ctx->launches += (ctx->tc ? 4 : 3) * steps;
             return AP_OK;
         }
     }
@@ -499,8 +545,10 @@ void free_all(ap_ctx* ctx) {
     cudaGetLastError();
 }
 
+int solve_width(const ap_ctx* ctx, int c) { return ctx->tc ? std::max(16, pad_c(c)) : pad_c(c); }
+
 ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev, float* W_dev, ap_info* info) {
-    const int Cp = pad_c(c);
+    const int Cp = solve_width(ctx, c);
     AP_TRY(ensure_solve(ctx, Cp));
     const int64_t want_trace = ctx->o.block_trace ? ctx->o.trace_cap : 0;
     if (want_trace > ctx->trace_alloc) {
@@ -516,6 +564,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
     ++ctx->launches;
     AP_CK(cudaMemsetAsync(ctx->step, 0, sizeof(int64_t), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
+    AP_CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st));
     // ||b_c|| for the relative residuals
     AP_TRY(launch_norms(ctx, ctx->Bp, kEpiColNorms));
     double bn[AP_MAX_RHS] = {}, rn[AP_MAX_RHS] = {};
@@ -558,11 +607,16 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         AP_TRY(run_epoch(ctx, ns));
         steps += ns;
         ++epoch;
-        int nanf = 0;
+        int nanf = 0, tcerr = 0;
         AP_CK(cudaMemcpyAsync(rn, ctx->colnorm, sizeof(double) * Cp, cudaMemcpyDeviceToHost, ctx->st));
         AP_CK(cudaMemcpyAsync(&nanf, ctx->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        AP_CK(cudaMemcpyAsync(&tcerr, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         AP_CK(cudaStreamSynchronize(ctx->st));
         collect_profile(ctx, ns);
+        if (tcerr) {
+            status = AP_ERR_TIMEOUT;
+            break;
+        }
         if (nanf) {
             status = AP_ERR_NAN;
             break;
@@ -709,7 +763,8 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     if (o->block < 1 || o->select < 0 || o->select > 2 || o->stop < 0 || o->stop > 3) return AP_ERR_INVALID_ARG;
     if (o->precision < 0 || o->precision > 2 || o->max_epochs < 1 || o->min_epochs < 0) return AP_ERR_INVALID_ARG;
     if (o->residual_mode < 0 || o->residual_mode > 2) return AP_ERR_INVALID_ARG;
-    if (o->precision != AP_FP32) return AP_ERR_UNSUPPORTED;
+    if (o->precision == AP_FP16_REFINE) return AP_ERR_UNSUPPORTED;
+    if (o->precision == AP_BF16_REFINE && d + 2 > 32) return AP_ERR_UNSUPPORTED;
     ap_ctx* ctx = new (std::nothrow) ap_ctx();
     if (!ctx) return AP_ERR_NOMEM;
     ctx->n = n;
@@ -723,6 +778,17 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     ctx->nt = (int)((ctx->b + kTile - 1) / kTile);
     ctx->ntri = (int64_t)ctx->nt * (ctx->nt + 1) / 2;
     ctx->ust = (cudaStream_t)o->stream;
+    ctx->tc = o->precision == AP_BF16_REFINE;
+    ctx->kd = tc_kd(d);
+    ctx->cpb = (int)((ctx->b + 63) / 64);
+    ctx->tps128 = (ctx->b + 127) / 128;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            ctx->num_sms = sms;
+        cudaGetLastError();
+    }
     ap_status s = AP_OK;
     auto fail = [&](ap_status e) {
         free_all(ctx);
@@ -746,7 +812,13 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     if ((s = dalloc_t(ctx, &ctx->step, 1)) != AP_OK) return fail(s);
     if ((s = dalloc_t(ctx, &ctx->nan_flag, 1)) != AP_OK) return fail(s);
     if ((s = dalloc_t(ctx, &ctx->bad, (size_t)ctx->m)) != AP_OK) return fail(s);
+    if ((s = dalloc_t(ctx, &ctx->tc_err, 1)) != AP_OK) return fail(s);
+    if (ctx->tc) {
+        if ((s = dalloc_t(ctx, &ctx->XA, tc_rows_bytes(ctx->m * ctx->tps128, ctx->kd))) != AP_OK) return fail(s);
+        if ((s = dalloc_t(ctx, &ctx->XB, tc_cols_bytes(ctx->m, ctx->cpb, ctx->kd))) != AP_OK) return fail(s);
+    }
     if (cudaMemset(ctx->ticket, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ctx->tc_err, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->sel, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return fail(AP_ERR_CUDA);

@@ -165,6 +165,30 @@ cudaError_t launch_assemble_v(const float* W, int C, const float* B, int c, int6
 cudaError_t launch_dot0(const float* W, int C, const float* Y, int cy, int64_t n, double* part, unsigned* ticket,
                        double* out, cudaStream_t st);
 
+// ---- tensor-core form of the residual update (kmv_tc.cu) -------------------
+struct TcParams;
+int tc_kd(int d);
+size_t tc_rows_bytes(int64_t ntiles, int kd);
+size_t tc_cols_bytes(int64_t m, int cpb, int kd);
+size_t tc_delta_bytes(int cpb, int C);
+cudaError_t launch_tc_pack_inputs(int kernel, const float* Xs, int64_t n, int d, int D, int64_t b, int64_t m,
+                                  int64_t tps, int cpb, int kd, uint8_t* XA, uint8_t* XB, cudaStream_t st);
+cudaError_t launch_tc_pack_delta(const float* Delta, int64_t b, int C, int cpb, uint8_t* DT, cudaStream_t st);
+struct TcLaunch {
+    const uint8_t* XA;
+    const uint8_t* XB;
+    const uint8_t* DT;
+    const float* Delta;
+    float* R;
+    int64_t n, b;
+    int cpb;
+    float s, noise;
+    const int* sel;
+    int* err;
+    EpiParams epi;
+};
+cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int grid, cudaStream_t st);
+
 // Read-only view of what the gradient kernel needs from a context.
 struct GradView {
     const float* Xs;

@@ -1,0 +1,720 @@
+// Tensor-core (tcgen05) form of the fused AP residual update (Eq. text_update_of_r)
+// with the Gauss-Southwell epilogue (Eq. approximate_gauss_southwell).
+//
+// Per 128-row tile of R and per 64-column chunk of the selected block I:
+//   1. S = [x_s | a | 1] [-2 x_s' | 1 | a']^T on the tensor cores, a = |x_s|^2, so
+//      S_ij = |x_s,i - x_s,j|^2 = t_ij directly (FP16 hi/lo operands, three
+//      products, FP32 accumulation in tensor memory);
+//   2. sixteen transform warps load t from tensor memory, evaluate phi on the
+//      SFU and write P = phi back to tensor memory as a BF16 hi/lo pair;
+//   3. acc += P Delta^T on the tensor cores with P read from tensor memory and
+//      Delta^T (BF16 hi/lo, staged per step) from shared memory: the three
+//      products hi*hi + hi*lo + lo*hi carry about 16 bits.
+// After the last chunk the accumulator (128 x C FP32) leaves tensor memory and
+// R_i -= s acc_i + sigma^2 Delta_i (index diagonal), with the block norms of the
+// new R written per tile for the ticketed last-CTA selection.
+//
+// Warp roles: warps 0-15 transform (warp w owns TMEM lanes 32 (w % 4).. and
+// columns 16 (w / 4).. of a chunk; four transform warps per scheduler hide the
+// SFU and tensor-memory latencies); warp 16 lane 0 issues the distance MMAs,
+// warp 17 lane 0 the contraction MMAs and warp 18 lane 0 the bulk copies, so
+// that no issuer waits behind another one's barriers.  The three hi/lo products of
+// the contraction accumulate into three separate accumulators (independent
+// MMA chains), summed in the epilogue.  Everything is double-buffered (S, P)
+// or ring-buffered (operand stages) and synchronised by mbarriers; every wait
+// is bounded in time and reports a timeout through the error flag instead of
+// hanging.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kmv_fp32.cuh"
+
+namespace ap {
+namespace tc {
+
+constexpr int kRows = 128;
+constexpr int kChunk = 64;
+constexpr int kStages = 6;
+constexpr int kXformWarps = 16;
+constexpr int kColsPerWarp = kChunk / (kXformWarps / 4);  // 16 columns of a chunk per warp
+constexpr int kLoadWarp = kXformWarps;       // distance MMAs (also owns the tensor memory)
+constexpr int kMmaWarp = kXformWarps + 1;    // contraction MMAs
+constexpr int kCopyWarp = kXformWarps + 2;   // bulk copies of the operand stages
+constexpr int kThreads = (kXformWarps + 3) * 32;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColS = 0;      // S[buf] at kColS + 64 buf
+constexpr uint32_t kColP = 128;    // P_hi[buf] at kColP + 64 buf, P_lo[buf] at + 32 (BF16 pairs)
+constexpr uint32_t kColAcc = 256;  // three accumulators (hi*hi, hi*lo, lo*hi), C columns each
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
+// the phase completes (or the hint expires) instead of spinning on the issue
+// slots the transform warps need.
+constexpr uint32_t kSuspendHintNs = 1000000;
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Gives up when the deadline passes or when
+// another thread of the CTA already gave up (abort flag), and reports it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(err_flag, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+        "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows
+// x 16 bytes stored contiguously (128 B); lbo = byte distance between core
+// matrices adjacent along K, sbo = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
+    return d;                // base offset 0, lbo mode 0, layout SWIZZLE_NONE (0)
+}
+
+// Instruction descriptor of kind::f16 / kind::tf32: FP32 accumulate, A/B types
+// (0 F16, 1 BF16, 2 TF32), both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_type, uint32_t M, uint32_t N) {
+    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// phi from the tensor-core distance t.  RBF operands carry the FP32 path's
+// scaling (t = r^2 log2(e) / 2, phi = 2^-t).  Matern operands are additionally
+// scaled by log2(e), so sqrt(t) = u log2(e) with u = sqrt(3 or 5) r, which puts
+// e^-u on the SFU without a multiply; the polynomial takes the 1/log2(e) powers.
+constexpr float kInvL = 0.69314718055994531f;                 // 1 / log2(e)
+constexpr float kInvL2Third = 0.69314718055994531f * 0.69314718055994531f / 3.0f;
+template <int KERN>
+__device__ __forceinline__ float phi_tc(float t) {
+    if constexpr (KERN == AP_RBF) {
+        return ex2_approx(-t);
+    } else if constexpr (KERN == AP_MATERN32) {
+        const float u = sqrt_approx(fabsf(t));
+        return fmaf(u, kInvL, 1.0f) * ex2_approx(-u);
+    } else {
+        const float u = sqrt_approx(fabsf(t));
+        return fmaf(u, fmaf(u, kInvL2Third, kInvL), 1.0f) * ex2_approx(-u);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+    return r;
+}
+
+__device__ __forceinline__ float bf16_lo_to_f32(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi_to_f32(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+}  // namespace tc
+
+// -------------------------------------------------------------- kernel params
+struct TcParams {
+    const uint8_t* XA;     // row operand tiles: ntiles x (2 x 128 x KD fp16)
+    const uint8_t* XB;     // column operand chunks: m x cpb x (2 x 64 x KD fp16)
+    const uint8_t* DT;     // Delta^T chunks of this step: cpb x (2 x C x 64 bf16)
+    const float* Delta;    // b x C FP32 (noise diagonal)
+    float* R;              // n x C
+    int64_t n, b;
+    int cpb;               // chunks per block
+    float s, noise;
+    const int* sel;
+    int* err;              // timeout flag
+    EpiParams epi;         // tiles of 128 rows aligned to blocks (tiles_per_seg = ceil(b / 128))
+};
+
+template <int KERN, int KD, int C>
+__global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams p) {
+    using namespace tc;
+    constexpr uint32_t kXaBytes = 2u * kRows * KD * 2u;   // hi + lo
+    constexpr uint32_t kXbBytes = 2u * kChunk * KD * 2u;  // hi + lo
+    constexpr uint32_t kDtBytes = 2u * C * kChunk * 2u;   // hi + lo
+    constexpr uint32_t kStageBytes = kXbBytes + kDtBytes;
+    constexpr int KSTEPS_D = KD / 16;
+
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint8_t* s_xa = tc_smem;                         // 2 buffers
+    uint8_t* s_stage = tc_smem + 2 * kXaBytes;       // kStages buffers
+    __shared__ __align__(8) uint64_t bar_stage_full[kStages], bar_stage_empty[kStages];
+    __shared__ __align__(8) uint64_t bar_xa_full[2], bar_xa_empty[2];
+    __shared__ __align__(8) uint64_t bar_s_full[2], bar_s_free[2], bar_p_full[2], bar_p_free[2];
+    __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_free;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ double red_d[32];
+    __shared__ int red_i[32];
+    __shared__ double s_colred[4][C];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const EpiParams& e = p.epi;
+
+    const int I = *p.sel;
+    const int64_t col0 = (int64_t)I * p.b;
+    const int64_t ncols = min(p.b, p.n - col0);
+    const int nq = (int)((ncols + kChunk - 1) / kChunk);
+    const int64_t ntiles = e.ntiles;
+    const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&bar_stage_full[i], 1);
+            mbar_init(&bar_stage_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_xa_full[i], 1);
+            mbar_init(&bar_xa_empty[i], 1);
+            mbar_init(&bar_s_full[i], 1);
+            mbar_init(&bar_s_free[i], kXformWarps);
+            mbar_init(&bar_p_full[i], kXformWarps);
+            mbar_init(&bar_p_free[i], 1);
+        }
+        mbar_init(&bar_acc_full, 1);
+        mbar_init(&bar_acc_free, 4);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kLoadWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == kCopyWarp) {
+        // ------------------------------------------------ bulk-copy issuer
+        if (lane == 0 && my_tiles > 0 && nq > 0) {
+            const int64_t total_chunks = my_tiles * nq;
+            auto issue_xa = [&](int64_t tt) -> bool {
+                const int xb = (int)(tt & 1);
+                const int64_t u = tt >> 1;
+                if (u >= 1 && !mbar_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1), &s_abort, p.err)) return false;
+                const int64_t tile = blockIdx.x + tt * gridDim.x;
+                mbar_expect_tx(&bar_xa_full[xb], kXaBytes);
+                bulk_g2s(s_xa + (size_t)xb * kXaBytes, p.XA + (size_t)tile * kXaBytes, kXaBytes, &bar_xa_full[xb]);
+                return true;
+            };
+            bool ok = issue_xa(0);
+            for (int64_t i = 0; i < total_chunks && ok; ++i) {
+                const int q = (int)(i % nq);
+                const int64_t tt = i / nq;
+                if (q == 0 && tt + 1 < my_tiles) ok = issue_xa(tt + 1);
+                const int s = (int)(i % kStages);
+                const int64_t u = i / kStages;
+                if (ok && u >= 1) ok = mbar_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1), &s_abort, p.err);
+                if (!ok) break;
+                uint8_t* dst = s_stage + (size_t)s * kStageBytes;
+                mbar_expect_tx(&bar_stage_full[s], kStageBytes);
+                bulk_g2s(dst, p.XB + ((size_t)I * p.cpb + q) * kXbBytes, kXbBytes, &bar_stage_full[s]);
+                bulk_g2s(dst + kXbBytes, p.DT + (size_t)q * kDtBytes, kDtBytes, &bar_stage_full[s]);
+            }
+        }
+    } else if (warp == kLoadWarp) {
+        // ------------------------------------------------ distance MMA issuer
+        if (lane == 0 && my_tiles > 0 && nq > 0) {
+            constexpr uint32_t idesc_d = instr_desc(0, kRows, kChunk);  // F16 x F16 -> F32, 128 x 64
+            bool ok = true;
+            int64_t g = 0;
+            for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
+                const int xb = (int)(tt & 1);
+                ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((tt >> 1) & 1), &s_abort, p.err);
+                const uint32_t xa_hi = smem_u32(s_xa + (size_t)xb * kXaBytes);
+                const uint32_t xa_lo = xa_hi + kXaBytes / 2;
+                for (int q = 0; q < nq && ok; ++q, ++g) {
+                    const int s = (int)(g % kStages);
+                    const int buf = (int)(g & 1);
+                    ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err);
+                    if (ok && g >= 2) ok = mbar_wait(&bar_s_free[buf], (uint32_t)(((g >> 1) - 1) & 1), &s_abort, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t xbh = smem_u32(s_stage + (size_t)s * kStageBytes);
+                    const uint32_t xbl = xbh + kXbBytes / 2;
+                    const uint32_t dS = tmem + kColS + 64u * buf;
+                    constexpr uint32_t sboA = (KD / 8) * 128;
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS_D; ++ks) {
+                        const uint32_t off = ks * 256;
+                        mma_ss(dS, smem_desc(xa_hi + off, 128, sboA), smem_desc(xbh + off, 128, sboA), idesc_d, acc);
+                        acc = 1;
+                        mma_ss(dS, smem_desc(xa_hi + off, 128, sboA), smem_desc(xbl + off, 128, sboA), idesc_d, 1);
+                        mma_ss(dS, smem_desc(xa_lo + off, 128, sboA), smem_desc(xbh + off, 128, sboA), idesc_d, 1);
+                    }
+                    tc_commit(&bar_s_full[buf]);
+                    if (q == nq - 1) tc_commit(&bar_xa_empty[xb]);
+                }
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------ contraction MMA issuer
+        if (lane == 0 && my_tiles > 0 && nq > 0) {
+            constexpr uint32_t idesc_c = instr_desc(1, kRows, C);  // BF16 x BF16 -> F32, 128 x C
+            bool ok = true;
+            int64_t g = 0;
+            for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
+                for (int q = 0; q < nq && ok; ++q, ++g) {
+                    const int buf = (int)(g & 1);
+                    const int s = (int)(g % kStages);
+                    ok = mbar_wait(&bar_p_full[buf], (uint32_t)((g >> 1) & 1), &s_abort, p.err);
+                    if (ok && q == 0 && tt >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((tt - 1) & 1), &s_abort, p.err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
+                    const uint32_t dtl = dth + kDtBytes / 2;
+                    const uint32_t pH = tmem + kColP + 64u * buf;
+                    const uint32_t pL = pH + 32u;
+                    const uint32_t a0 = tmem + kColAcc, a1 = a0 + C, a2 = a0 + 2 * C;
+                    // K-step of 16 BF16 values = 8 tensor-memory columns of P, two 16-byte
+                    // core columns of Delta^T (core columns 128 B apart, row groups 1 KB)
+#pragma unroll
+                    for (int ks = 0; ks < kChunk / 16; ++ks) {
+                        const uint32_t acc = (q == 0 && ks == 0) ? 0u : 1u;
+                        const uint32_t boff = ks * 256;
+                        mma_ts(a0, pH + 8u * ks, smem_desc(dth + boff, 128, 1024), idesc_c, acc);
+                        mma_ts(a1, pH + 8u * ks, smem_desc(dtl + boff, 128, 1024), idesc_c, acc);
+                        mma_ts(a2, pL + 8u * ks, smem_desc(dth + boff, 128, 1024), idesc_c, acc);
+                    }
+                    tc_commit(&bar_p_free[buf]);
+                    tc_commit(&bar_stage_empty[s]);
+                    if (q == nq - 1) tc_commit(&bar_acc_full);
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ transform warps
+        // Software pipelined: while chunk g is transformed, the tensor-memory load
+        // of chunk g + 1 is already in flight.
+        const int quarter = warp & 3, group = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const int64_t total = my_tiles * nq;
+        bool ok = total > 0;
+        uint32_t ta[kColsPerWarp], tb[kColsPerWarp];
+        auto s_addr = [&](int64_t g) -> uint32_t {
+            return tmem + lane_base + kColS + 64u * (uint32_t)(g & 1) + (uint32_t)(kColsPerWarp * group);
+        };
+        // tile epilogue (warps 0-3, one row per thread); it always passes both
+        // named barriers so that a failed wait cannot strand the other warps
+        auto epilogue = [&](int64_t tt) {
+            const int64_t tile = blockIdx.x + tt * gridDim.x;
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(tt & 1), &s_abort, p.err));
+            if (ok) tc_fence_after();
+            const int64_t segi = tile / e.tiles_per_seg;
+            const int64_t seg_lo = segi * e.seg;
+            const int64_t seg_hi = min(seg_lo + e.seg, p.n);
+            const int64_t r0 = seg_lo + (tile % e.tiles_per_seg) * kRows;
+            const int64_t i = r0 + quarter * 32 + lane;
+            const bool live = ok && i < seg_hi;
+            const bool diag = i >= col0 && i < col0 + ncols;
+            double sq = 0.0;
+            // 16 columns at a time: sum the three accumulators, update R, norms
+#pragma unroll 1
+            for (int c0 = 0; c0 < C; c0 += 16) {
+                float a16[16];
+                if (ok) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + kColAcc + c0, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) a16[k] = __uint_as_float(r[k]);
+                    tmem_ld16(tmem + lane_base + kColAcc + C + c0, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+                    tmem_ld16(tmem + lane_base + kColAcc + 2 * C + c0, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    float v = 0.0f;
+                    if (live) {
+                        const int c = c0 + k;
+                        v = fmaf(-p.s, a16[k], p.R[i * C + c]);
+                        if (diag) v = fmaf(-p.noise, p.Delta[(i - col0) * C + c], v);
+                        p.R[i * C + c] = v;
+                        sq += (double)v * (double)v;
+                    }
+                    if (e.flags & kEpiColNorms) {
+                        double w = (double)v * (double)v;
+                        for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
+                        if (lane == 0) s_colred[warp][c0 + k] = w;
+                    }
+                }
+            }
+            if (ok) tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_acc_free);
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+            if (lane == 0) red_d[warp] = sq;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (tid == 0) {
+                e.part_norm[tile] = red_d[0] + red_d[1] + red_d[2] + red_d[3];
+                if (e.flags & kEpiColNorms)
+                    for (int c = 0; c < C; ++c)
+                        e.part_col[tile * C + c] = s_colred[0][c] + s_colred[1][c] + s_colred[2][c] + s_colred[3][c];
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        };
+        // one chunk: S of chunk g is in `cur` (load issued), prefetch g + 1 into `nxt`
+        auto chunk = [&](int64_t g, uint32_t (&cur)[kColsPerWarp], uint32_t (&nxt)[kColsPerWarp]) {
+            const int buf = (int)(g & 1);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_s_free[buf]);
+            if (g + 1 < total) {
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(&bar_s_full[buf ^ 1], (uint32_t)(((g + 1) >> 1) & 1), &s_abort, p.err));
+                if (ok) {
+                    tc_fence_after();
+                    tmem_ld16(s_addr(g + 1), nxt);
+                }
+            }
+            uint32_t ph[kColsPerWarp / 2], pl[kColsPerWarp / 2];
+#pragma unroll
+            for (int k = 0; k < kColsPerWarp / 2; ++k) {
+                const float v0 = phi_tc<KERN>(__uint_as_float(cur[2 * k]));
+                const float v1 = phi_tc<KERN>(__uint_as_float(cur[2 * k + 1]));
+                const uint32_t h = pack_bf16(v0, v1);
+                ph[k] = h;
+                pl[k] = pack_bf16(v0 - bf16_lo_to_f32(h), v1 - bf16_hi_to_f32(h));
+            }
+            if (ok && g >= 2)
+                ok = __all_sync(0xffffffffu, mbar_wait(&bar_p_free[buf], (uint32_t)(((g >> 1) - 1) & 1), &s_abort, p.err));
+            if (ok) {
+                tc_fence_after();
+                tmem_st8(tmem + lane_base + kColP + 64u * buf + (uint32_t)(kColsPerWarp / 2 * group), ph);
+                tmem_st8(tmem + lane_base + kColP + 64u * buf + 32u + (uint32_t)(kColsPerWarp / 2 * group), pl);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_p_full[buf]);
+            }
+            if (warp < 4 && (g % nq) == nq - 1) epilogue(g / nq);
+        };
+        if (ok) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[0], 0u, &s_abort, p.err));
+            if (ok) {
+                tc_fence_after();
+                tmem_ld16(s_addr(0), ta);
+            }
+        }
+        for (int64_t g = 0; g < total && ok; g += 2) {
+            chunk(g, ta, tb);
+            if (ok && g + 1 < total) chunk(g + 1, tb, ta);
+        }
+        tmem_wait_ld();
+    }
+    // ---------------------------------------------------------- teardown
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kLoadWarp) {
+        if (s_abort) {
+            // a wait gave up: give bulk copies and MMAs still in flight time to land
+            // before the tensor memory and the shared buffers are released
+            const long long t0 = clock64();
+            while (clock64() - t0 < 4000000LL) {
+            }
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    if (s_abort) return;  // a wait gave up: leave R and the selection as they are, err is set
+    // tiles with no CTA (ntiles < grid) write nothing; CTAs without tiles still take a ticket
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(e.ticket, 1u) == gridDim.x - 1u) ? 1 : 0;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        epi_finalize<C>(e, red_d, red_i);
+    }
+}
+
+// ---------------------------------------------------------- operand packing
+namespace {
+
+// byte offset of element (row, k) of a K-major, no-swizzle operand with KD
+// columns: core matrices of 8 rows x 8 halves, K-adjacent cores 128 B apart.
+__device__ __forceinline__ size_t core_off(int row, int k, int kd) {
+    return ((size_t)((row >> 3) * (kd >> 3) + (k >> 3)) * 8 + (row & 7)) * 16 + (size_t)(k & 7) * 2;
+}
+
+__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+}
+
+// Row operand tiles: [x_s | a | 1 | 0...] for the rows of every block-aligned tile.
+__global__ void pack_rows_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int64_t tps,
+                                 int KD, float fold, uint8_t* __restrict__ XA) {
+    const int64_t tile = blockIdx.x;
+    const int64_t seg_lo = (tile / tps) * b;
+    const int64_t seg_hi = min(seg_lo + b, n);
+    const int64_t r0 = seg_lo + (tile % tps) * 128;
+    const size_t half_bytes = (size_t)128 * KD * 2;
+    uint8_t* dst = XA + (size_t)tile * 2 * half_bytes;
+    for (int t = threadIdx.x; t < 128 * KD; t += blockDim.x) {
+        const int row = t / KD, k = t % KD;
+        const int64_t i = r0 + row;
+        float v = 0.0f;
+        if (i < seg_hi) {
+            if (k < d) {
+                v = (float)((double)Xs[i * D + k] * fold);
+            } else if (k == d) {
+                double a = 0.0;
+                for (int q = 0; q < d; ++q) a += (double)Xs[i * D + q] * (double)Xs[i * D + q];
+                v = (float)(a * fold * fold);
+            } else if (k == d + 1) {
+                v = 1.0f;
+            }
+        }
+        __half hi, lo;
+        split_f16(v, hi, lo);
+        const size_t off = core_off(row, k, KD);
+        *reinterpret_cast<__half*>(dst + off) = hi;
+        *reinterpret_cast<__half*>(dst + half_bytes + off) = lo;
+    }
+}
+
+// Column operand chunks: [-2 x_s | 1 | a | 0...] for 64 columns per chunk, per block.
+__global__ void pack_cols_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int cpb, int KD,
+                                 float fold, uint8_t* __restrict__ XB) {
+    const int64_t chunk = blockIdx.x;  // block * cpb + q
+    const int64_t blk = chunk / cpb;
+    const int q = (int)(chunk % cpb);
+    const int64_t lo_col = blk * b, hi_col = min(lo_col + b, n);
+    const size_t half_bytes = (size_t)64 * KD * 2;
+    uint8_t* dst = XB + (size_t)chunk * 2 * half_bytes;
+    for (int t = threadIdx.x; t < 64 * KD; t += blockDim.x) {
+        const int row = t / KD, k = t % KD;
+        const int64_t j = lo_col + (int64_t)q * 64 + row;
+        float v = 0.0f;
+        if (j < hi_col) {
+            if (k < d) {
+                v = (float)(-2.0 * (double)Xs[j * D + k] * fold);
+            } else if (k == d) {
+                v = 1.0f;
+            } else if (k == d + 1) {
+                double a = 0.0;
+                for (int s = 0; s < d; ++s) a += (double)Xs[j * D + s] * (double)Xs[j * D + s];
+                v = (float)(a * fold * fold);
+            }
+        }
+        __half hi, lo;
+        split_f16(v, hi, lo);
+        const size_t off = core_off(row, k, KD);
+        *reinterpret_cast<__half*>(dst + off) = hi;
+        *reinterpret_cast<__half*>(dst + half_bytes + off) = lo;
+    }
+}
+
+// Delta^T chunks of the current step: C rows (right-hand sides) x 64 columns
+// (block-local points) as BF16 hi/lo, K-major core matrices of 8 rows x 8
+// halves (8 K-cores per row group).
+__global__ void pack_delta_kernel(const float* __restrict__ Delta, int64_t b, int C, int cpb, uint8_t* __restrict__ DT) {
+    const int q = blockIdx.x;
+    const size_t half_bytes = (size_t)C * 64 * 2;
+    uint8_t* dst = DT + (size_t)q * 2 * half_bytes;
+    for (int t = threadIdx.x; t < C * 64; t += blockDim.x) {
+        const int c = t / 64, k = t % 64;  // row c, K index k
+        const int64_t li = (int64_t)q * 64 + k;
+        const float v = li < b ? Delta[li * C + c] : 0.0f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const size_t off = ((size_t)((c >> 3) * 8 + (k >> 3)) * 8 + (c & 7)) * 16 + (size_t)(k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(dst + off) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(dst + half_bytes + off) = lo;
+    }
+}
+
+template <int KERN, int KD, int C>
+cudaError_t launch_tc_inst(const TcParams& p, int grid, cudaStream_t st) {
+    constexpr size_t xa = 2u * 128 * KD * 2u, xb = 2u * 64 * KD * 2u, dt = 2u * C * 64 * 2u;
+    const size_t smem = 2 * xa + tc::kStages * (xb + dt) + 1024;
+    auto fn = kmv_tc_kernel<KERN, KD, C>;
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    fn<<<grid, tc::kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_kd(int d) { return d + 2 <= 16 ? 16 : 32; }
+
+size_t tc_rows_bytes(int64_t ntiles, int kd) { return (size_t)ntiles * 2 * 128 * kd * 2; }
+size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * 2 * 64 * kd * 2; }
+size_t tc_delta_bytes(int cpb, int C) { return (size_t)cpb * 2 * C * 64 * 2; }
+
+cudaError_t launch_tc_pack_inputs(int kernel, const float* Xs, int64_t n, int d, int D, int64_t b, int64_t m,
+                                  int64_t tps, int cpb, int kd, uint8_t* XA, uint8_t* XB, cudaStream_t st) {
+    const float fold = kernel == AP_RBF ? 1.0f : 1.4426950408889634f;
+    pack_rows_kernel<<<(unsigned)(m * tps), 256, 0, st>>>(Xs, n, d, D, b, tps, kd, fold, XA);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    pack_cols_kernel<<<(unsigned)(m * cpb), 256, 0, st>>>(Xs, n, d, D, b, cpb, kd, fold, XB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pack_delta(const float* Delta, int64_t b, int C, int cpb, uint8_t* DT, cudaStream_t st) {
+    pack_delta_kernel<<<cpb, 256, 0, st>>>(Delta, b, C, cpb, DT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kmv_tc(int kernel, const TcParams& p, int kd, int C, int grid, cudaStream_t st) {
+#define AP_TC_K(KK)                                                         \
+    if (kd == 16 && C == 16) return launch_tc_inst<KK, 16, 16>(p, grid, st); \
+    if (kd == 16 && C == 32) return launch_tc_inst<KK, 16, 32>(p, grid, st); \
+    if (kd == 32 && C == 16) return launch_tc_inst<KK, 32, 16>(p, grid, st); \
+    if (kd == 32 && C == 32) return launch_tc_inst<KK, 32, 32>(p, grid, st); \
+    return cudaErrorInvalidValue;
+    switch (kernel) {
+        case AP_RBF: { AP_TC_K(AP_RBF) }
+        case AP_MATERN32: { AP_TC_K(AP_MATERN32) }
+        case AP_MATERN52: { AP_TC_K(AP_MATERN52) }
+        default: return cudaErrorInvalidValue;
+    }
+#undef AP_TC_K
+}
+
+cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int grid, cudaStream_t st) {
+    TcParams p;
+    p.XA = l.XA;
+    p.XB = l.XB;
+    p.DT = l.DT;
+    p.Delta = l.Delta;
+    p.R = l.R;
+    p.n = l.n;
+    p.b = l.b;
+    p.cpb = l.cpb;
+    p.s = l.s;
+    p.noise = l.noise;
+    p.sel = l.sel;
+    p.err = l.err;
+    p.epi = l.epi;
+    return launch_kmv_tc(kernel, p, kd, C, grid, st);
+}
+
+}  // namespace ap
