@@ -431,6 +431,43 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args) -> None:
+    """Replay the serving workload: Poisson arrivals at `rate`/s, n log-uniform in
+    [2^10, 2^18], d in {3..20}, RBF or Matern-5/2, tolerance 1e-2 or 1e-4, half of
+    the requests in the tensor-core form; each request = solve + posterior mean
+    on 1024 test points; admitted by a 120 GB HBM budget."""
+    import paper_2310_17137_gb300 as ap
+    trace = wl.serving_trace(n_requests=args.serve_requests, rate=args.serve_rate)
+    data = [wl.request_data(r, m_test=1024) for r in trace]
+    srv = ap.ApServer(hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    t0 = time.perf_counter()
+    ids = []
+    for r, (X, y, Xt) in zip(trace, data):
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        h = ap.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise, 0.0)
+        prec = ap.AP_BF16_REFINE if r.low_precision else ap.AP_FP32
+        ids.append(srv.submit(X, y, Xt, h, block=min(r.n, 4096), tol=r.tol, stop=ap.AP_STOP_Y_REL, min_epochs=1,
+                              max_epochs=args.serve_max_epochs, precision=prec))
+    res = [srv.wait(i, timeout_s=3600.0) for i in ids]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([x["latency_s"] for x in res])
+    entries = sum(float(r.n) ** 2 * max(1, x["epochs"]) for r, x in zip(trace, res))
+    line = {"metric": METRIC, "mode": "serving", "value": len(res) / wall, "unit": "solves/s",
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_queue_s": float(np.mean([x["queue_s"] for x in res])), "wall_s": wall,
+            "requests": len(res), "converged": int(sum(x["status"] == ap.AP_OK for x in res)),
+            "kernel_entries_per_s": entries / wall,
+            "config": {"workload": f"{len(res)} requests, Poisson {args.serve_rate}/s, n logU[2^10, 2^18], "
+                                   "d U{3..20}, RBF or Matern-5/2, tol {1e-2, 1e-4}, solve + mean on 1024 "
+                                   "test points, half in the tensor-core form",
+                       "hbm_budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
+                       "max_epochs": args.serve_max_epochs, "stop": "y column"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap_ = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap_.add_argument("--gpus", type=int, default=1)
@@ -448,10 +485,19 @@ def main():
     ap_.add_argument("--no-cpu-baseline", action="store_true")
     ap_.add_argument("--no-e2e", action="store_true")
     ap_.add_argument("--no-ttt", action="store_true")
+    ap_.add_argument("--serve", action="store_true", help="replay the serving workload instead")
+    ap_.add_argument("--serve-requests", type=int, default=512)
+    ap_.add_argument("--serve-rate", type=float, default=40.0)
+    ap_.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap_.add_argument("--serve-slots", type=int, default=8)
+    ap_.add_argument("--serve-max-epochs", type=int, default=30)
     args = ap_.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
-    if args.impl == "reference":
+    if args.serve:
+        if rank == 0:
+            run_serving(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world)

@@ -230,6 +230,59 @@ ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const f
 /* Number of kernels this context has launched since ap_create (all calls). */
 int64_t ap_launch_count(const ap_ctx* ctx);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of GP solve + posterior-mean requests (no counterpart in
+ * the paper, which solves one system at a time): requests are admitted in
+ * arrival order as soon as a worker slot is free and the request's estimated
+ * device footprint fits in the HBM budget; each admitted request runs its own
+ * context (cache, Alg. 1 with one CUDA graph per epoch, posterior mean) on its
+ * worker's stream, so requests overlap on the device.  Results are
+ * deterministic: the same alone and in a mix. */
+typedef struct ap_server ap_server;
+
+/* One request.  All host buffers are owned by the caller and must stay valid
+ * until the request is done (inputs are copied to the device when the request
+ * starts; mean_host is written when it finishes). */
+typedef struct ap_request {
+    const float* X_host;      /* n x d training inputs */
+    int64_t n;
+    int32_t d;
+    const float* y_host;      /* n labels; the solve is K_hat w = y - hyper.mean */
+    const float* Xtest_host;  /* M x d test inputs */
+    int64_t M;
+    ap_hyper hyper;           /* lengthscales copied at submit */
+    int64_t block;
+    double tol;
+    int32_t stop;             /* ap_stop */
+    int32_t min_epochs;
+    int32_t max_epochs;
+    int32_t precision;        /* ap_precision */
+    int32_t refine_every;
+    float* mean_host;         /* out: M posterior means */
+} ap_request;
+
+typedef struct ap_request_result {
+    int32_t done;             /* 1 once finished */
+    ap_status status;         /* of the solve (OK, NOT_CONVERGED, ...) once done */
+    int32_t epochs;
+    double rel_res;           /* ||r||/||y - mu|| reported by the solve */
+    double queue_s;           /* submit -> start */
+    double latency_s;         /* submit -> result written */
+    size_t reserved_bytes;    /* HBM reserved for the request while it runs */
+} ap_request_result;
+
+/* Start a server on device `device` with `slots` worker streams and an HBM
+ * budget in bytes.  Errors: INVALID_ARG, CUDA. */
+ap_status ap_server_create(ap_server** out, size_t hbm_budget, int32_t slots, int32_t device);
+/* Queue a request; *id identifies it.  NOMEM if it can never fit the budget. */
+ap_status ap_server_submit(ap_server* srv, const ap_request* req, int64_t* id);
+/* Non-blocking status of a request. */
+ap_status ap_server_poll(ap_server* srv, int64_t id, ap_request_result* res);
+/* Wait up to timeout_s seconds for a request; TIMEOUT if it is not done. */
+ap_status ap_server_wait(ap_server* srv, int64_t id, double timeout_s, ap_request_result* res);
+/* Finish admitted requests, drop the rest, stop the workers. */
+void ap_server_destroy(ap_server* srv);
+
 /* Release everything the context owns.  NULL is allowed. */
 void ap_destroy(ap_ctx* ctx);
 
@@ -240,6 +293,8 @@ const char* ap_status_str(ap_status s);
 size_t ap_sizeof_opts(void);
 size_t ap_sizeof_info(void);
 size_t ap_sizeof_hyper(void);
+size_t ap_sizeof_request(void);
+size_t ap_sizeof_request_result(void);
 
 #ifdef __cplusplus
 }

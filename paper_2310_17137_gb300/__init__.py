@@ -27,7 +27,7 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_IN
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_grad_quadforms_static", "MLLDataFit"]
+           "ap_status_str", "ap_launch_count", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
 
 
 class ApError(RuntimeError):
@@ -223,6 +223,71 @@ def ap_destroy(ctx: Context) -> None:
     if ctx is not None and ctx.handle:
         _capi.load().ap_destroy(ctx.handle)
         ctx.handle = None
+
+
+class ApServer:
+    """Continuous-batching server (ap_server_*): GP solve + posterior mean per
+    request, admitted by HBM budget, overlapping on the device.  Keeps the
+    host arrays of every request alive until the server is closed."""
+
+    def __init__(self, hbm_budget: int, slots: int = 4, device: int = 0):
+        self.L = _capi.load()
+        self.handle = ctypes.c_void_p()
+        st = self.L.ap_server_create(ctypes.byref(self.handle), int(hbm_budget), int(slots), int(device))
+        if st != AP_OK:
+            raise ApError(st, "ap_server_create")
+        self._keep = {}
+
+    def submit(self, X, y, Xtest, hyper: Hyper, block: int = 4096, tol: float = 1e-2,
+               stop: int = AP_STOP_MAX_REL, min_epochs: int = 1, max_epochs: int = 1000,
+               precision: int = AP_FP32, refine_every: int = 4) -> int:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32).ravel()
+        Xt = np.ascontiguousarray(Xtest, dtype=np.float32)
+        mean = np.zeros(Xt.shape[0], dtype=np.float32)
+        h, ell = hyper.to_c()
+        r = _capi.ap_request(X.ctypes.data, X.shape[0], X.shape[1], y.ctypes.data, Xt.ctypes.data, Xt.shape[0],
+                             h, int(block), float(tol), int(stop), int(min_epochs), int(max_epochs),
+                             int(precision), int(refine_every), mean.ctypes.data)
+        rid = ctypes.c_int64(0)
+        st = self.L.ap_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid))
+        if st != AP_OK:
+            raise ApError(st, "ap_server_submit")
+        self._keep[rid.value] = (X, y, Xt, mean, ell)
+        return rid.value
+
+    @staticmethod
+    def _res(res) -> dict:
+        return dict(done=bool(res.done), status=res.status, epochs=res.epochs, rel_res=res.rel_res,
+                    queue_s=res.queue_s, latency_s=res.latency_s, reserved_bytes=res.reserved_bytes)
+
+    def poll(self, rid: int) -> dict:
+        res = _capi.ap_request_result()
+        st = self.L.ap_server_poll(self.handle, int(rid), ctypes.byref(res))
+        if st != AP_OK:
+            raise ApError(st, "ap_server_poll")
+        return self._res(res)
+
+    def wait(self, rid: int, timeout_s: float = 600.0) -> dict:
+        res = _capi.ap_request_result()
+        st = self.L.ap_server_wait(self.handle, int(rid), float(timeout_s), ctypes.byref(res))
+        if st != AP_OK:
+            raise ApError(st, "ap_server_wait")
+        return self._res(res)
+
+    def mean(self, rid: int) -> np.ndarray:
+        return self._keep[rid][3]
+
+    def close(self) -> None:
+        if self.handle:
+            self.L.ap_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MLLDataFit:

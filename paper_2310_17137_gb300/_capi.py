@@ -24,7 +24,8 @@ AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED = 0, 1, 2
 EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_residual",
            "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy", "ap_status_str",
            "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count",
-           "ap_grad_quadforms_static"]
+           "ap_grad_quadforms_static", "ap_server_create", "ap_server_submit", "ap_server_poll",
+           "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result"]
 
 
 class ap_hyper(ctypes.Structure):
@@ -52,6 +53,20 @@ class ap_info(ctypes.Structure):
                 ("entries_per_s", ctypes.c_double), ("gpu_launches", ctypes.c_int64),
                 ("data_fit", ctypes.c_double), ("t_update_s", ctypes.c_double),
                 ("n_update", ctypes.c_int64), ("t_blocksolve_s", ctypes.c_double)]
+
+
+class ap_request(ctypes.Structure):
+    _fields_ = [("X_host", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("y_host", ctypes.c_void_p), ("Xtest_host", ctypes.c_void_p), ("M", ctypes.c_int64),
+                ("hyper", ap_hyper), ("block", ctypes.c_int64), ("tol", ctypes.c_double),
+                ("stop", ctypes.c_int32), ("min_epochs", ctypes.c_int32), ("max_epochs", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("refine_every", ctypes.c_int32), ("mean_host", ctypes.c_void_p)]
+
+
+class ap_request_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int), ("epochs", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double),
+                ("reserved_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -86,10 +101,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_mll_grad": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
         "ap_destroy": (None, [P]),
         "ap_launch_count": (i64, [P]),
+        "ap_server_create": (st, [ctypes.POINTER(P), ctypes.c_size_t, i32, i32]),
+        "ap_server_submit": (st, [P, ctypes.POINTER(ap_request), ctypes.POINTER(i64)]),
+        "ap_server_poll": (st, [P, i64, ctypes.POINTER(ap_request_result)]),
+        "ap_server_wait": (st, [P, i64, ctypes.c_double, ctypes.POINTER(ap_request_result)]),
+        "ap_server_destroy": (None, [P]),
         "ap_status_str": (ctypes.c_char_p, [st]),
         "ap_sizeof_opts": (ctypes.c_size_t, []),
         "ap_sizeof_info": (ctypes.c_size_t, []),
         "ap_sizeof_hyper": (ctypes.c_size_t, []),
+        "ap_sizeof_request": (ctypes.c_size_t, []),
+        "ap_sizeof_request_result": (ctypes.c_size_t, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

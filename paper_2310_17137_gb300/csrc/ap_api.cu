@@ -101,7 +101,9 @@ ap_status dalloc(ap_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     if (ctx->o.hbm_budget && ctx->bytes + bytes > ctx->o.hbm_budget) return AP_ERR_NOMEM;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    // stream-ordered allocation on the context stream: no device-wide
+    // synchronisation, so concurrent contexts (serving) keep running
+    if (cudaMallocAsync(p, bytes, ctx->st) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return AP_ERR_NOMEM;
@@ -124,7 +126,7 @@ void dfree(ap_ctx* ctx, T*& p) {
         ctx->bytes -= it->second;
         ctx->sizes.erase(it);
     }
-    cudaFree((void*)p);
+    cudaFreeAsync((void*)p, ctx->st);
     p = nullptr;
 }
 
@@ -529,7 +531,8 @@ void free_all(ap_ctx* ctx) {
     drop_graph(ctx);
     std::vector<void*> ptrs;
     for (auto& kv : ctx->sizes) ptrs.push_back(kv.first);
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, ctx->st);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
     ctx->sizes.clear();
     ctx->bytes = 0;
     if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
@@ -817,9 +820,9 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
         if ((s = dalloc_t(ctx, &ctx->XA, tc_rows_bytes(ctx->m * ctx->tps128, ctx->kd))) != AP_OK) return fail(s);
         if ((s = dalloc_t(ctx, &ctx->XB, tc_cols_bytes(ctx->m, ctx->cpb, ctx->kd))) != AP_OK) return fail(s);
     }
-    if (cudaMemset(ctx->ticket, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(ctx->tc_err, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->sel, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMemsetAsync(ctx->ticket, 0, 4 * sizeof(unsigned), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->sel, 0, sizeof(int), ctx->st) != cudaSuccess) {
         cudaGetLastError();
         return fail(AP_ERR_CUDA);
     }

@@ -39,6 +39,8 @@ def test_struct_layouts_match_binding(lib):
     assert lib.ap_sizeof_opts() == ctypes.sizeof(_capi.ap_opts)
     assert lib.ap_sizeof_info() == ctypes.sizeof(_capi.ap_info)
     assert lib.ap_sizeof_hyper() == ctypes.sizeof(_capi.ap_hyper)
+    assert lib.ap_sizeof_request() == ctypes.sizeof(_capi.ap_request)
+    assert lib.ap_sizeof_request_result() == ctypes.sizeof(_capi.ap_request_result)
 
 
 def test_defaults_and_status_strings(lib):
