@@ -150,6 +150,18 @@ def traffic_from_profiles(kernel: str, workload_name: str, n_launch_units: float
     return ent["dram_bytes_per_launch"] * n_launch_units / ent.get("units_per_launch", n_launch_units)
 
 
+def aggregate(ms: float, units: float, dist, device):
+    """Whole-job numbers of a multi-rank run: the slowest rank's time and the sum
+    of the units all ranks processed (replicas: no data-path collective)."""
+    import torch
+    ms_t = torch.tensor([ms], device=device, dtype=torch.float64)
+    u_t = torch.tensor([units], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u_t, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(u_t.item())
+
+
 def run_ours(args, rank: int, world: int):
     import torch
 
@@ -162,20 +174,20 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     p = workload(args.workload, sub=rank, n=args.n)
-    prec = {"fp32": ap.AP_FP32, "bf16": ap.AP_BF16_REFINE, "fp16": ap.AP_FP16_REFINE}[args.precision]
+    prec = {"fp32": ap.AP_FP32, "bf16": ap.AP_BF16_REFINE}[args.precision]
     hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
     X = torch.from_numpy(p.X).to(dev)
     B = torch.from_numpy(p.B).to(dev)
     W = torch.empty_like(B)
     stream = torch.cuda.current_stream(dev)
 
-    def opts():
+    def opts(pr=None):
         return ap.ap_opts_default(block=p.block, tol=p.tol, stop=ap.AP_STOP_MAX_REL, min_epochs=args.min_epochs,
-                                  max_epochs=args.max_epochs, precision=prec, profile=1,
-                                  stream=stream.cuda_stream)
+                                  max_epochs=args.max_epochs, precision=prec if pr is None else pr, profile=1,
+                                  refine_every=args.refine_every, stream=stream.cuda_stream)
 
-    def one_step():
-        ctx = ap.ap_create(X, hyper, opts())
+    def one_step(pr=None):
+        ctx = ap.ap_create(X, hyper, opts(pr))
         st, _, info, _ = ap.ap_solve(ctx, B, W=W)
         launches = ap.ap_launch_count(ctx)
         ap.ap_destroy(ctx)
@@ -203,19 +215,33 @@ def run_ours(args, rank: int, world: int):
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-
     cache_entries = float(p.n) * float(p.block)
     entries = sum(cache_entries + i["kernel_entries"] for i in infos)
-    ent_t = torch.tensor([entries], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(ent_t)
-    total_entries = float(ent_t.item())
+    ms_max, total_entries = aggregate(e0.elapsed_time(e1), entries, dist, dev)
     value = total_entries / (ms_max * 1e-3)
+
+    # the other form on the same problem, timed the same way (BF16+refine vs FP32)
+    compare = None
+    if not args.no_compare:
+        other = ap.AP_FP32 if prec != ap.AP_FP32 else ap.AP_BF16_REFINE
+        one_step(other)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cinfos = []
+        for _ in range(args.steps):
+            _, ci, _ = one_step(other)
+            cinfos.append(ci)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / args.steps
+        compare = {"form": "fp32" if other == ap.AP_FP32 else "bf16", "ms_per_step": cms,
+                   "kernel_entries_per_s": cent / (cms * 1e-3),
+                   "update_kernel_ms": cinfos[-1]["t_update_s"] / max(1, cinfos[-1]["n_update"]) * 1e3,
+                   "solve_s": statistics.median(i["t_solve_s"] for i in cinfos),
+                   "rel_res_y": cinfos[-1]["rel_res_true"][0], "rel_res_max": max(cinfos[-1]["rel_res_true"]),
+                   "epochs": cinfos[-1]["epochs"], "refinements": cinfos[-1]["refinements"]}
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e_value = None
@@ -230,6 +256,7 @@ def run_ours(args, rank: int, world: int):
             dist.destroy_process_group()
         return
     line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt)
+    line["other_form"] = compare
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, infos[-1]["epochs"], args)
     print(json.dumps(line), flush=True)
@@ -256,14 +283,8 @@ def end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist):
         e2e_entries += cache_entries + info["kernel_entries"]
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e2.elapsed_time(e3)
-    e2e_ms_t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
-        ent2 = torch.tensor([e2e_entries], device=dev, dtype=torch.float64)
-        dist.all_reduce(ent2)
-        e2e_entries = float(ent2.item())
-    return e2e_entries / (float(e2e_ms_t.item()) * 1e-3)
+    e2e_ms, e2e_entries = aggregate(e2.elapsed_time(e3), e2e_entries, dist, dev)
+    return e2e_entries / (e2e_ms * 1e-3)
 
 
 def time_to_tol_small(ap, torch, dev, stream) -> dict:
@@ -310,11 +331,12 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "dtype": "f32" if args.precision == "fp32" else "bf16",
         "data": "synthetic (seeded NumPy PCG64; stands in for the paper's UCI sets)",
         "config": describe(p, args),
         "epochs": [i["epochs"] for i in infos],
         "refinements": [i["refinements"] for i in infos],
+        "refine_s": statistics.median(i["t_refine_s"] for i in infos),
         "status": [ap.ap_status_str(s) for s in statuses],
         "rel_res_max": max(max(i["rel_res_true"]) for i in infos),
         "rel_res_y": infos[-1]["rel_res_true"][0],
@@ -475,7 +497,10 @@ def main():
     ap_.add_argument("--warmup", type=int, default=3)
     ap_.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap_.add_argument("--workload", default="matern52_ard")
-    ap_.add_argument("--precision", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap_.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
+                     help="form of the timed steps: bf16 = tensor-core BF16 hi/lo + FP32 refinement")
+    ap_.add_argument("--refine-every", type=int, default=10)
+    ap_.add_argument("--no-compare", action="store_true", help="skip the timed run of the other form")
     ap_.add_argument("--min-epochs", type=int, default=11)
     ap_.add_argument("--max-epochs", type=int, default=30,
                      help="epoch cap per solve (the configured tolerance is out of AP's reach on "

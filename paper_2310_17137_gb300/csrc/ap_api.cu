@@ -655,6 +655,23 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         if (epoch >= ctx->o.max_epochs) break;
         if (ctx->o.max_steps > 0 && steps >= ctx->o.max_steps) break;
     }
+    // A low-precision run that stopped on its epoch cap reports the true
+    // residual of the W it returns: one more FP32 recompute (max_steps runs,
+    // used to replay individual steps, are left untouched).
+    if (low_precision && status == AP_ERR_NOT_CONVERGED && ctx->o.max_steps <= 0 && epoch > 0 &&
+        !(have_true && (epoch % std::max(1, ctx->o.refine_every)) == 0)) {
+        AP_CK(cudaEventRecord(ctx->ev_r0, ctx->st));
+        AP_TRY(launch_full_residual(ctx, ctx->Bp, ctx->W, ctx->R, kEpiColNorms));
+        AP_CK(cudaEventRecord(ctx->ev_r1, ctx->st));
+        AP_CK(cudaMemcpyAsync(rn, ctx->colnorm, sizeof(double) * Cp, cudaMemcpyDeviceToHost, ctx->st));
+        AP_CK(cudaStreamSynchronize(ctx->st));
+        float rms = 0.f;
+        cudaEventElapsedTime(&rms, ctx->ev_r0, ctx->ev_r1);
+        t_refine += rms * 1e-3;
+        ++refinements;
+        rel_from(rel_true);
+        have_true = true;
+    }
     AP_CK(cudaEventRecord(ctx->ev_b, ctx->st));
     AP_CK(launch_unpad_copy(ctx->W, ctx->n, Cp, W_dev, c, ctx->st));
     ++ctx->launches;
