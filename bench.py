@@ -128,9 +128,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_src_hash() -> str:
+KERNEL_SOURCES = {"kmv_fp32_update": ["kmv_fp32.cuh", "ap_internal.cuh"],
+                  "kmv_tc_update": ["kmv_tc.cu", "kmv_fp32.cuh", "ap_internal.cuh"]}
+
+
+def kernel_src_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for fn in ["kmv_fp32.cuh", "ap_internal.cuh"]:
+    for fn in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2310_17137_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -145,7 +149,7 @@ def traffic_from_profiles(kernel: str, workload_name: str, n_launch_units: float
     with open(path) as f:
         t = json.load(f)
     ent = t.get(f"{kernel}:{workload_name}")
-    if not ent or ent.get("src_hash") != kernel_src_hash():
+    if not ent or ent.get("src_hash") != kernel_src_hash(kernel):
         return None
     return ent["dram_bytes_per_launch"] * n_launch_units / ent.get("units_per_launch", n_launch_units)
 
