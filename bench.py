@@ -39,6 +39,9 @@ import numpy as np  # noqa: E402
 import workloads as wl  # noqa: E402
 
 METRIC = "AP time-to-tol & kernel-entries/s, BF16+refine vs FP32; serve p50/p99"
+# forms of the residual update: FP32 SIMT, tensor-core BF16 hi/lo
+FORMS = {"fp32": lambda ap: ap.AP_FP32, "bf16": lambda ap: ap.AP_BF16_REFINE}
+DTYPES = {"fp32": "f32", "bf16": "bf16"}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 
@@ -140,7 +143,7 @@ def kernel_src_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel: str, workload_name: str, n_launch_units: float):
+def traffic_from_profiles(kernel: str, workload_name: str, precision: str, n_launch_units: float):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
     or None when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -148,7 +151,7 @@ def traffic_from_profiles(kernel: str, workload_name: str, n_launch_units: float
         return None
     with open(path) as f:
         t = json.load(f)
-    ent = t.get(f"{kernel}:{workload_name}")
+    ent = t.get(f"{kernel}:{workload_name}:{precision}")
     if not ent or ent.get("src_hash") != kernel_src_hash(kernel):
         return None
     return ent["dram_bytes_per_launch"] * n_launch_units / ent.get("units_per_launch", n_launch_units)
@@ -178,7 +181,7 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     p = workload(args.workload, sub=rank, n=args.n)
-    prec = {"fp32": ap.AP_FP32, "bf16": ap.AP_BF16_REFINE}[args.precision]
+    prec = FORMS[args.precision](ap)
     hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
     X = torch.from_numpy(p.X).to(dev)
     B = torch.from_numpy(p.B).to(dev)
@@ -224,28 +227,32 @@ def run_ours(args, rank: int, world: int):
     ms_max, total_entries = aggregate(e0.elapsed_time(e1), entries, dist, dev)
     value = total_entries / (ms_max * 1e-3)
 
-    # the other form on the same problem, timed the same way (BF16+refine vs FP32)
+    # the other forms on the same problem, timed the same way
     compare = None
     if not args.no_compare:
-        other = ap.AP_FP32 if prec != ap.AP_FP32 else ap.AP_BF16_REFINE
-        one_step(other)
-        torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        cinfos = []
-        for _ in range(args.steps):
-            _, ci, _ = one_step(other)
-            cinfos.append(ci)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1) / args.steps
-        cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / args.steps
-        compare = {"form": "fp32" if other == ap.AP_FP32 else "bf16", "ms_per_step": cms,
-                   "kernel_entries_per_s": cent / (cms * 1e-3),
-                   "update_kernel_ms": cinfos[-1]["t_update_s"] / max(1, cinfos[-1]["n_update"]) * 1e3,
-                   "solve_s": statistics.median(i["t_solve_s"] for i in cinfos),
-                   "rel_res_y": cinfos[-1]["rel_res_true"][0], "rel_res_max": max(cinfos[-1]["rel_res_true"]),
-                   "epochs": cinfos[-1]["epochs"], "refinements": cinfos[-1]["refinements"]}
+        compare = {}
+        for name in FORMS:
+            if name == args.precision:
+                continue
+            other = FORMS[name](ap)
+            one_step(other)
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            cinfos = []
+            for _ in range(args.steps):
+                _, ci, _ = one_step(other)
+                cinfos.append(ci)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1) / args.steps
+            cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / args.steps
+            compare[name] = {"ms_per_step": cms, "kernel_entries_per_s": cent / (cms * 1e-3),
+                             "update_kernel_ms": cinfos[-1]["t_update_s"] / max(1, cinfos[-1]["n_update"]) * 1e3,
+                             "solve_s": statistics.median(i["t_solve_s"] for i in cinfos),
+                             "rel_res_y": cinfos[-1]["rel_res_true"][0],
+                             "rel_res_max": max(cinfos[-1]["rel_res_true"]),
+                             "epochs": cinfos[-1]["epochs"], "refinements": cinfos[-1]["refinements"]}
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e_value = None
@@ -260,7 +267,7 @@ def run_ours(args, rank: int, world: int):
             dist.destroy_process_group()
         return
     line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt)
-    line["other_form"] = compare
+    line["other_forms"] = compare
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, infos[-1]["epochs"], args)
     print(json.dumps(line), flush=True)
@@ -335,7 +342,7 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic (seeded NumPy PCG64; stands in for the paper's UCI sets)",
         "config": describe(p, args),
         "epochs": [i["epochs"] for i in infos],
@@ -374,7 +381,7 @@ def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
         peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": traffic_from_profiles("kmv_fp32_update", args.workload, units),
+                "traffic": traffic_from_profiles("kmv_fp32_update", args.workload, "fp32", units),
                 "kernel": "kmv_fp32_kernel (fused residual update, one AP step)",
                 "per_unit": f"{flops_per_entry} FP32 flop per kernel entry (2c contraction + 3d distance)",
                 "peak_note": f"FP32 FMA pipe: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
@@ -384,10 +391,12 @@ def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
     peak = NUM_SMS * SFU_OPS_PER_SM * sm_max * 1e6 / 1e12
     kd = 16 if p.d + 2 <= 16 else 32
     cp = max(16, p.c)
+    # distance: three FP16 hi/lo products of K = kd; contraction: three BF16 hi/lo
+    # products of K = 1 per entry and C columns
     tensor_flops = 3 * 2 * kd + 3 * 2 * cp
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_from_profiles("kmv_tc_update", args.workload, units),
+            "traffic": traffic_from_profiles("kmv_tc_update", args.workload, args.precision, units),
             "kernel": "kmv_tc_kernel (tcgen05 fused residual update, one AP step)",
             "per_unit": f"{mufu} SFU (MUFU) op per kernel entry; units are tera-ops/s of the SFU pipe",
             "peak_note": f"SFU pipe: {NUM_SMS} SMs x {SFU_OPS_PER_SM} results/clk x {sm_max:.0f} MHz "
@@ -501,10 +510,11 @@ def main():
     ap_.add_argument("--warmup", type=int, default=3)
     ap_.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap_.add_argument("--workload", default="matern52_ard")
-    ap_.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
-                     help="form of the timed steps: bf16 = tensor-core BF16 hi/lo + FP32 refinement")
+    ap_.add_argument("--precision", choices=sorted(FORMS), default="bf16",
+                     help="form of the timed steps: bf16 = tensor-core BF16 hi/lo with FP32 refinement, "
+                          "fp32 = FP32 SIMT")
     ap_.add_argument("--refine-every", type=int, default=10)
-    ap_.add_argument("--no-compare", action="store_true", help="skip the timed run of the other form")
+    ap_.add_argument("--no-compare", action="store_true", help="skip the timed runs of the other forms")
     ap_.add_argument("--min-epochs", type=int, default=11)
     ap_.add_argument("--max-epochs", type=int, default=30,
                      help="epoch cap per solve (the configured tolerance is out of AP's reach on "

@@ -64,7 +64,12 @@ typedef enum { AP_RBF = 0, AP_MATERN32 = 1, AP_MATERN52 = 2 } ap_kernel;
  *                    operands and FP32 accumulation; accuracy recovered by
  *                    recomputing R = B - K_hat W in the FP32 form (iterative
  *                    refinement, justified by the residual lemma of App. B).
- *   AP_FP16_REFINE:  as above with FP16 operands. */
+ *   AP_FP16_REFINE:  reserved; ap_create returns AP_ERR_UNSUPPORTED.  One FP16
+ *                    product (11-bit kernel values) perturbs K_hat by about
+ *                    2^-12 sqrt(n) max|K_ij| in norm, which exceeds sigma^2 at
+ *                    the sizes this library targets (n = 262,144, sigma^2 =
+ *                    1e-2), so the perturbed operator is not positive definite
+ *                    and the iteration diverges. */
 typedef enum { AP_FP32 = 0, AP_BF16_REFINE = 1, AP_FP16_REFINE = 2 } ap_precision;
 
 /* Block selection (Sec. 3, "Block Selection"): Gauss-Southwell on

@@ -800,7 +800,7 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     ctx->ust = (cudaStream_t)o->stream;
     ctx->tc = o->precision == AP_BF16_REFINE;
     ctx->kd = tc_kd(d);
-    ctx->cpb = (int)((ctx->b + 63) / 64);
+    ctx->cpb = tc_chunks_per_block(ctx->b);
     ctx->tps128 = (ctx->b + 127) / 128;
     {
         int dev = 0, sms = 0;

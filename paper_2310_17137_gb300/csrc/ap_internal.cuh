@@ -168,6 +168,7 @@ cudaError_t launch_dot0(const float* W, int C, const float* Y, int cy, int64_t n
 // ---- tensor-core form of the residual update (kmv_tc.cu) -------------------
 struct TcParams;
 int tc_kd(int d);
+int tc_chunks_per_block(int64_t b);
 size_t tc_rows_bytes(int64_t ntiles, int kd);
 size_t tc_cols_bytes(int64_t m, int cpb, int kd);
 size_t tc_delta_bytes(int cpb, int C);

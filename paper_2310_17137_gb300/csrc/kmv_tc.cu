@@ -1,12 +1,13 @@
 // Tensor-core (tcgen05) form of the fused AP residual update (Eq. text_update_of_r)
 // with the Gauss-Southwell epilogue (Eq. approximate_gauss_southwell).
 //
-// Per 128-row tile of R and per 64-column chunk of the selected block I:
+// Per 128-row tile of R and per 128-column chunk of the selected block I:
 //   1. S = [x_s | a | 1] [-2 x_s' | 1 | a']^T on the tensor cores, a = |x_s|^2, so
 //      S_ij = |x_s,i - x_s,j|^2 = t_ij directly (FP16 hi/lo operands, three
 //      products, FP32 accumulation in tensor memory);
 //   2. sixteen transform warps load t from tensor memory, evaluate phi on the
-//      SFU and write P = phi back to tensor memory as a BF16 hi/lo pair;
+//      SFU and write P = phi back as a BF16 hi/lo pair, in place: every 16
+//      FP32 columns of S become 8 columns of P_hi followed by 8 of P_lo;
 //   3. acc += P Delta^T on the tensor cores with P read from tensor memory and
 //      Delta^T (BF16 hi/lo, staged per step) from shared memory: the three
 //      products hi*hi + hi*lo + lo*hi carry about 16 bits.
@@ -15,15 +16,16 @@
 // new R written per tile for the ticketed last-CTA selection.
 //
 // Warp roles: warps 0-15 transform (warp w owns TMEM lanes 32 (w % 4).. and
-// columns 16 (w / 4).. of a chunk; four transform warps per scheduler hide the
-// SFU and tensor-memory latencies); warp 16 lane 0 issues the distance MMAs,
-// warp 17 lane 0 the contraction MMAs and warp 18 lane 0 the bulk copies, so
-// that no issuer waits behind another one's barriers.  The three hi/lo products of
-// the contraction accumulate into three separate accumulators (independent
-// MMA chains), summed in the epilogue.  Everything is double-buffered (S, P)
-// or ring-buffered (operand stages) and synchronised by mbarriers; every wait
-// is bounded in time and reports a timeout through the error flag instead of
-// hanging.
+// columns 32 (w / 4).. of a chunk, in two halves of 16; four transform warps per
+// scheduler hide the SFU and tensor-memory latencies); warp 16 lane 0 issues
+// the distance MMAs, warp 17 lane 0 the contraction MMAs and warp 18 lane 0 the
+// bulk copies, so that no issuer waits behind another one's barriers.  The
+// three hi/lo products of the contraction accumulate into three separate
+// accumulators (independent MMA chains), summed in the epilogue.  S/P live in a
+// ring of three tensor-memory buffers (a buffer is reused once the contraction
+// that read its P has completed), operands in a ring of shared-memory stages;
+// everything is synchronised by mbarriers, and every wait is bounded in time
+// and reports a timeout through the error flag instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -33,18 +35,18 @@ namespace ap {
 namespace tc {
 
 constexpr int kRows = 128;
-constexpr int kChunk = 64;
-constexpr int kStages = 6;
+constexpr int kChunk = 128;  // columns of the block per chunk
+constexpr int kStages = 4;
+constexpr int kBufs = 3;     // S/P tensor-memory buffers
 constexpr int kXformWarps = 16;
-constexpr int kColsPerWarp = kChunk / (kXformWarps / 4);  // 16 columns of a chunk per warp
+constexpr int kColsPerWarp = kChunk / (kXformWarps / 4);  // 32 columns of a chunk per warp
 constexpr int kLoadWarp = kXformWarps;       // distance MMAs (also owns the tensor memory)
 constexpr int kMmaWarp = kXformWarps + 1;    // contraction MMAs
 constexpr int kCopyWarp = kXformWarps + 2;   // bulk copies of the operand stages
 constexpr int kThreads = (kXformWarps + 3) * 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColS = 0;      // S[buf] at kColS + 64 buf
-constexpr uint32_t kColP = 128;    // P_hi[buf] at kColP + 64 buf, P_lo[buf] at + 32 (BF16 pairs)
-constexpr uint32_t kColAcc = 256;  // three accumulators (hi*hi, hi*lo, lo*hi), C columns each
+constexpr uint32_t kColAcc = kBufs * kChunk;  // three accumulators (hi*hi, hi*lo, lo*hi), C columns each
+static_assert(kColAcc + 3 * 32 <= kTmemCols, "tensor memory budget");
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------ PTX helpers
@@ -198,18 +200,6 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_type, uint32_t M, 
 // e^-u on the SFU without a multiply; the polynomial takes the 1/log2(e) powers.
 constexpr float kInvL = 0.69314718055994531f;                 // 1 / log2(e)
 constexpr float kInvL2Third = 0.69314718055994531f * 0.69314718055994531f / 3.0f;
-template <int KERN>
-__device__ __forceinline__ float phi_tc(float t) {
-    if constexpr (KERN == AP_RBF) {
-        return ex2_approx(-t);
-    } else if constexpr (KERN == AP_MATERN32) {
-        const float u = sqrt_approx(fabsf(t));
-        return fmaf(u, kInvL, 1.0f) * ex2_approx(-u);
-    } else {
-        const float u = sqrt_approx(fabsf(t));
-        return fmaf(u, fmaf(u, kInvL2Third, kInvL), 1.0f) * ex2_approx(-u);
-    }
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
     uint32_t r;
@@ -220,13 +210,64 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 __device__ __forceinline__ float bf16_lo_to_f32(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi_to_f32(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
+// Paired FP32 arithmetic (one instruction for two lanes of a float2, each lane
+// rounded exactly as the scalar operation).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// phi of two distances at once: the SFU work per lane, the polynomial paired.
+template <int KERN>
+__device__ __forceinline__ float2 phi_tc2(float t0, float t1) {
+    if constexpr (KERN == AP_RBF) {
+        return make_float2(ex2_approx(-t0), ex2_approx(-t1));
+    } else {
+        const float2 u = make_float2(sqrt_approx(fabsf(t0)), sqrt_approx(fabsf(t1)));
+        const float2 ex = make_float2(ex2_approx(-u.x), ex2_approx(-u.y));
+        const float2 one = make_float2(1.0f, 1.0f);
+        float2 poly;
+        if constexpr (KERN == AP_MATERN32) {
+            poly = fma2(u, make_float2(kInvL, kInvL), one);
+        } else {
+            poly = fma2(u, fma2(u, make_float2(kInvL2Third, kInvL2Third), make_float2(kInvL, kInvL)), one);
+        }
+        return mul2(poly, ex);
+    }
+}
+
 }  // namespace tc
 
 // -------------------------------------------------------------- kernel params
 struct TcParams {
     const uint8_t* XA;     // row operand tiles: ntiles x (2 x 128 x KD fp16)
-    const uint8_t* XB;     // column operand chunks: m x cpb x (2 x 64 x KD fp16)
-    const uint8_t* DT;     // Delta^T chunks of this step: cpb x (2 x C x 64 bf16)
+    const uint8_t* XB;     // column operand chunks: m x cpb x (2 x 128 x KD fp16)
+    const uint8_t* DT;     // Delta^T chunks of this step: cpb x (2 x C x 128 bf16)
     const float* Delta;    // b x C FP32 (noise diagonal)
     float* R;              // n x C
     int64_t n, b;
@@ -245,13 +286,18 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     constexpr uint32_t kDtBytes = 2u * C * kChunk * 2u;   // hi + lo
     constexpr uint32_t kStageBytes = kXbBytes + kDtBytes;
     constexpr int KSTEPS_D = KD / 16;
+    constexpr int KSTEPS_C = kChunk / 16;
+    constexpr uint32_t kSboX = (KD / 8) * 128;      // 8-row groups of the X operands
+    constexpr uint32_t kSboD = (kChunk / 8) * 128;  // 8-row groups of Delta^T
 
     extern __shared__ __align__(1024) uint8_t tc_smem[];
     uint8_t* s_xa = tc_smem;                         // 2 buffers
     uint8_t* s_stage = tc_smem + 2 * kXaBytes;       // kStages buffers
     __shared__ __align__(8) uint64_t bar_stage_full[kStages], bar_stage_empty[kStages];
     __shared__ __align__(8) uint64_t bar_xa_full[2], bar_xa_empty[2];
-    __shared__ __align__(8) uint64_t bar_s_full[2], bar_s_free[2], bar_p_full[2], bar_p_free[2];
+    // per S/P buffer: S written (distance MMAs), P written (transform warps),
+    // P consumed (contraction MMAs)
+    __shared__ __align__(8) uint64_t bar_s_full[kBufs], bar_p_full[kBufs], bar_buf_free[kBufs];
     __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_free;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -279,10 +325,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_xa_full[i], 1);
             mbar_init(&bar_xa_empty[i], 1);
+        }
+        for (int i = 0; i < kBufs; ++i) {
             mbar_init(&bar_s_full[i], 1);
-            mbar_init(&bar_s_free[i], kXformWarps);
             mbar_init(&bar_p_full[i], kXformWarps);
-            mbar_init(&bar_p_free[i], 1);
+            mbar_init(&bar_buf_free[i], 1);
         }
         mbar_init(&bar_acc_full, 1);
         mbar_init(&bar_acc_free, 4);
@@ -314,9 +361,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 return true;
             };
             bool ok = issue_xa(0);
+            int q = 0;
+            int64_t tt = 0;
             for (int64_t i = 0; i < total_chunks && ok; ++i) {
-                const int q = (int)(i % nq);
-                const int64_t tt = i / nq;
                 if (q == 0 && tt + 1 < my_tiles) ok = issue_xa(tt + 1);
                 const int s = (int)(i % kStages);
                 const int64_t u = i / kStages;
@@ -326,12 +373,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 mbar_expect_tx(&bar_stage_full[s], kStageBytes);
                 bulk_g2s(dst, p.XB + ((size_t)I * p.cpb + q) * kXbBytes, kXbBytes, &bar_stage_full[s]);
                 bulk_g2s(dst + kXbBytes, p.DT + (size_t)q * kDtBytes, kDtBytes, &bar_stage_full[s]);
+                if (++q == nq) {
+                    q = 0;
+                    ++tt;
+                }
             }
         }
     } else if (warp == kLoadWarp) {
         // ------------------------------------------------ distance MMA issuer
         if (lane == 0 && my_tiles > 0 && nq > 0) {
-            constexpr uint32_t idesc_d = instr_desc(0, kRows, kChunk);  // F16 x F16 -> F32, 128 x 64
+            constexpr uint32_t idesc_d = instr_desc(0, kRows, kChunk);  // F16 x F16 -> F32, 128 x 128
             bool ok = true;
             int64_t g = 0;
             for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
@@ -341,23 +392,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 const uint32_t xa_lo = xa_hi + kXaBytes / 2;
                 for (int q = 0; q < nq && ok; ++q, ++g) {
                     const int s = (int)(g % kStages);
-                    const int buf = (int)(g & 1);
+                    const int buf = (int)(g % kBufs);
+                    const int64_t use = g / kBufs;
                     ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err);
-                    if (ok && g >= 2) ok = mbar_wait(&bar_s_free[buf], (uint32_t)(((g >> 1) - 1) & 1), &s_abort, p.err);
+                    if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t xbh = smem_u32(s_stage + (size_t)s * kStageBytes);
                     const uint32_t xbl = xbh + kXbBytes / 2;
-                    const uint32_t dS = tmem + kColS + 64u * buf;
-                    constexpr uint32_t sboA = (KD / 8) * 128;
+                    const uint32_t dS = tmem + (uint32_t)(kChunk * buf);
                     uint32_t acc = 0;
 #pragma unroll
                     for (int ks = 0; ks < KSTEPS_D; ++ks) {
                         const uint32_t off = ks * 256;
-                        mma_ss(dS, smem_desc(xa_hi + off, 128, sboA), smem_desc(xbh + off, 128, sboA), idesc_d, acc);
+                        mma_ss(dS, smem_desc(xa_hi + off, 128, kSboX), smem_desc(xbh + off, 128, kSboX), idesc_d, acc);
                         acc = 1;
-                        mma_ss(dS, smem_desc(xa_hi + off, 128, sboA), smem_desc(xbl + off, 128, sboA), idesc_d, 1);
-                        mma_ss(dS, smem_desc(xa_lo + off, 128, sboA), smem_desc(xbh + off, 128, sboA), idesc_d, 1);
+                        mma_ss(dS, smem_desc(xa_hi + off, 128, kSboX), smem_desc(xbl + off, 128, kSboX), idesc_d, 1);
+                        mma_ss(dS, smem_desc(xa_lo + off, 128, kSboX), smem_desc(xbh + off, 128, kSboX), idesc_d, 1);
                     }
                     tc_commit(&bar_s_full[buf]);
                     if (q == nq - 1) tc_commit(&bar_xa_empty[xb]);
@@ -372,28 +423,29 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             int64_t g = 0;
             for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
                 for (int q = 0; q < nq && ok; ++q, ++g) {
-                    const int buf = (int)(g & 1);
+                    const int buf = (int)(g % kBufs);
                     const int s = (int)(g % kStages);
-                    ok = mbar_wait(&bar_p_full[buf], (uint32_t)((g >> 1) & 1), &s_abort, p.err);
+                    ok = mbar_wait(&bar_p_full[buf], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
                     if (ok && q == 0 && tt >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((tt - 1) & 1), &s_abort, p.err);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
                     const uint32_t dtl = dth + kDtBytes / 2;
-                    const uint32_t pH = tmem + kColP + 64u * buf;
-                    const uint32_t pL = pH + 32u;
+                    const uint32_t pb = tmem + (uint32_t)(kChunk * buf);
                     const uint32_t a0 = tmem + kColAcc, a1 = a0 + C, a2 = a0 + 2 * C;
-                    // K-step of 16 BF16 values = 8 tensor-memory columns of P, two 16-byte
-                    // core columns of Delta^T (core columns 128 B apart, row groups 1 KB)
+                    // K-step ks: 16 BF16 values of P = 8 columns of P_hi at 16 ks and 8
+                    // of P_lo at 16 ks + 8; two 16-byte core columns of Delta^T (core
+                    // columns 128 B apart)
 #pragma unroll
-                    for (int ks = 0; ks < kChunk / 16; ++ks) {
+                    for (int ks = 0; ks < KSTEPS_C; ++ks) {
                         const uint32_t acc = (q == 0 && ks == 0) ? 0u : 1u;
                         const uint32_t boff = ks * 256;
-                        mma_ts(a0, pH + 8u * ks, smem_desc(dth + boff, 128, 1024), idesc_c, acc);
-                        mma_ts(a1, pH + 8u * ks, smem_desc(dtl + boff, 128, 1024), idesc_c, acc);
-                        mma_ts(a2, pL + 8u * ks, smem_desc(dth + boff, 128, 1024), idesc_c, acc);
+                        const uint32_t pH = pb + 16u * ks, pL = pH + 8u;
+                        mma_ts(a0, pH, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
+                        mma_ts(a1, pH, smem_desc(dtl + boff, 128, kSboD), idesc_c, acc);
+                        mma_ts(a2, pL, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
                     }
-                    tc_commit(&bar_p_free[buf]);
+                    tc_commit(&bar_buf_free[buf]);
                     tc_commit(&bar_stage_empty[s]);
                     if (q == nq - 1) tc_commit(&bar_acc_full);
                 }
@@ -401,15 +453,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         }
     } else {
         // ------------------------------------------------ transform warps
-        // Software pipelined: while chunk g is transformed, the tensor-memory load
-        // of chunk g + 1 is already in flight.
+        // Work unit = half a warp's columns of a chunk (16 entries per thread).
+        // Software pipelined: while unit u is transformed, the tensor-memory load
+        // of unit u + 1 is already in flight.
         const int quarter = warp & 3, group = warp >> 2;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        const int64_t total = my_tiles * nq;
+        const int total = (int)(my_tiles * nq);  // chunks of this CTA (< 2^31)
         bool ok = total > 0;
-        uint32_t ta[kColsPerWarp], tb[kColsPerWarp];
-        auto s_addr = [&](int64_t g) -> uint32_t {
-            return tmem + lane_base + kColS + 64u * (uint32_t)(g & 1) + (uint32_t)(kColsPerWarp * group);
+        uint32_t ta[16], tb[16];
+        // columns of unit (chunk c, half h): S there is replaced by [P_hi | P_lo]
+        auto u_addr = [&](int c, int h) -> uint32_t {
+            return tmem + lane_base + (uint32_t)(kChunk * (c % kBufs) + kColsPerWarp * group + 16 * h);
         };
         // tile epilogue (warps 0-3, one row per thread); it always passes both
         // named barriers so that a failed wait cannot strand the other warps
@@ -475,53 +529,60 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             }
             asm volatile("bar.sync 1, 128;" ::: "memory");
         };
-        // one chunk: S of chunk g is in `cur` (load issued), prefetch g + 1 into `nxt`
-        auto chunk = [&](int64_t g, uint32_t (&cur)[kColsPerWarp], uint32_t (&nxt)[kColsPerWarp]) {
-            const int buf = (int)(g & 1);
+        int q_in_tile = 0;  // chunk index within the current tile
+        int64_t tile_no = 0;
+        // one unit: S of (c, h) is in `cur` (load issued); prefetch the next unit
+        // into `nxt`, transform, store P in place; after the second half of a chunk
+        // signal the contraction MMA
+        auto unit = [&](int c, int h, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
             tmem_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_s_free[buf]);
-            if (g + 1 < total) {
-                ok = __all_sync(0xffffffffu,
-                                mbar_wait(&bar_s_full[buf ^ 1], (uint32_t)(((g + 1) >> 1) & 1), &s_abort, p.err));
+            if (h == 0) {
+                if (ok) tmem_ld16(u_addr(c, 1), nxt);
+            } else if (c + 1 < total) {
+                if (ok)
+                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[(c + 1) % kBufs],
+                                                          (uint32_t)(((c + 1) / kBufs) & 1), &s_abort, p.err));
                 if (ok) {
                     tc_fence_after();
-                    tmem_ld16(s_addr(g + 1), nxt);
+                    tmem_ld16(u_addr(c + 1, 0), nxt);
                 }
             }
-            uint32_t ph[kColsPerWarp / 2], pl[kColsPerWarp / 2];
+            uint32_t pw[16];  // [P_hi words | P_lo words]
 #pragma unroll
-            for (int k = 0; k < kColsPerWarp / 2; ++k) {
-                const float v0 = phi_tc<KERN>(__uint_as_float(cur[2 * k]));
-                const float v1 = phi_tc<KERN>(__uint_as_float(cur[2 * k + 1]));
-                const uint32_t h = pack_bf16(v0, v1);
-                ph[k] = h;
-                pl[k] = pack_bf16(v0 - bf16_lo_to_f32(h), v1 - bf16_hi_to_f32(h));
+            for (int k = 0; k < 8; ++k) {
+                const float2 v = phi_tc2<KERN>(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
+                const uint32_t hw = pack_bf16(v.x, v.y);
+                pw[k] = hw;
+                const float2 lo = sub2(v, make_float2(bf16_lo_to_f32(hw), bf16_hi_to_f32(hw)));
+                pw[8 + k] = pack_bf16(lo.x, lo.y);
             }
-            if (ok && g >= 2)
-                ok = __all_sync(0xffffffffu, mbar_wait(&bar_p_free[buf], (uint32_t)(((g >> 1) - 1) & 1), &s_abort, p.err));
-            if (ok) {
-                tc_fence_after();
-                tmem_st8(tmem + lane_base + kColP + 64u * buf + (uint32_t)(kColsPerWarp / 2 * group), ph);
-                tmem_st8(tmem + lane_base + kColP + 64u * buf + 32u + (uint32_t)(kColsPerWarp / 2 * group), pl);
-                tmem_wait_st();
-                tc_fence_before();
+            if (ok) tmem_st16(u_addr(c, h), pw);
+            if (h == 1) {
+                if (ok) {
+                    tmem_wait_st();
+                    tc_fence_before();
+                }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_p_full[buf]);
+                if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs]);
+                if (++q_in_tile == nq) {
+                    if (warp < 4) epilogue(tile_no);
+                    q_in_tile = 0;
+                    ++tile_no;
+                }
             }
-            if (warp < 4 && (g % nq) == nq - 1) epilogue(g / nq);
         };
         if (ok) {
             ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[0], 0u, &s_abort, p.err));
             if (ok) {
                 tc_fence_after();
-                tmem_ld16(s_addr(0), ta);
+                tmem_ld16(u_addr(0, 0), ta);
             }
         }
-        for (int64_t g = 0; g < total && ok; g += 2) {
-            chunk(g, ta, tb);
-            if (ok && g + 1 < total) chunk(g + 1, tb, ta);
+        // every chunk is visited even after a failed wait (without touching tensor
+        // memory), so warps 0-3 make the same number of epilogue calls
+        for (int c = 0; c < total; ++c) {
+            unit(c, 0, ta, tb);
+            unit(c, 1, tb, ta);
         }
         tmem_wait_ld();
     }
@@ -598,18 +659,18 @@ __global__ void pack_rows_kernel(const float* __restrict__ Xs, int64_t n, int d,
     }
 }
 
-// Column operand chunks: [-2 x_s | 1 | a | 0...] for 64 columns per chunk, per block.
+// Column operand chunks: [-2 x_s | 1 | a | 0...] for 128 columns per chunk, per block.
 __global__ void pack_cols_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int cpb, int KD,
                                  float fold, uint8_t* __restrict__ XB) {
     const int64_t chunk = blockIdx.x;  // block * cpb + q
     const int64_t blk = chunk / cpb;
     const int q = (int)(chunk % cpb);
     const int64_t lo_col = blk * b, hi_col = min(lo_col + b, n);
-    const size_t half_bytes = (size_t)64 * KD * 2;
+    const size_t half_bytes = (size_t)tc::kChunk * KD * 2;
     uint8_t* dst = XB + (size_t)chunk * 2 * half_bytes;
-    for (int t = threadIdx.x; t < 64 * KD; t += blockDim.x) {
+    for (int t = threadIdx.x; t < tc::kChunk * KD; t += blockDim.x) {
         const int row = t / KD, k = t % KD;
-        const int64_t j = lo_col + (int64_t)q * 64 + row;
+        const int64_t j = lo_col + (int64_t)q * tc::kChunk + row;
         float v = 0.0f;
         if (j < hi_col) {
             if (k < d) {
@@ -630,20 +691,21 @@ __global__ void pack_cols_kernel(const float* __restrict__ Xs, int64_t n, int d,
     }
 }
 
-// Delta^T chunks of the current step: C rows (right-hand sides) x 64 columns
+// Delta^T chunks of the current step: C rows (right-hand sides) x 128 columns
 // (block-local points) as BF16 hi/lo, K-major core matrices of 8 rows x 8
-// halves (8 K-cores per row group).
+// halves (16 K-cores per row group).
 __global__ void pack_delta_kernel(const float* __restrict__ Delta, int64_t b, int C, int cpb, uint8_t* __restrict__ DT) {
     const int q = blockIdx.x;
-    const size_t half_bytes = (size_t)C * 64 * 2;
+    const size_t half_bytes = (size_t)C * tc::kChunk * 2;
     uint8_t* dst = DT + (size_t)q * 2 * half_bytes;
-    for (int t = threadIdx.x; t < C * 64; t += blockDim.x) {
-        const int c = t / 64, k = t % 64;  // row c, K index k
-        const int64_t li = (int64_t)q * 64 + k;
+    for (int t = threadIdx.x; t < C * tc::kChunk; t += blockDim.x) {
+        const int c = t / tc::kChunk, k = t % tc::kChunk;  // row c, K index k
+        const int64_t li = (int64_t)q * tc::kChunk + k;
         const float v = li < b ? Delta[li * C + c] : 0.0f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const size_t off = ((size_t)((c >> 3) * 8 + (k >> 3)) * 8 + (c & 7)) * 16 + (size_t)(k & 7) * 2;
+        const size_t off =
+            ((size_t)((c >> 3) * (tc::kChunk / 8) + (k >> 3)) * 8 + (c & 7)) * 16 + (size_t)(k & 7) * 2;
         *reinterpret_cast<__nv_bfloat16*>(dst + off) = hi;
         *reinterpret_cast<__nv_bfloat16*>(dst + half_bytes + off) = lo;
     }
@@ -651,7 +713,7 @@ __global__ void pack_delta_kernel(const float* __restrict__ Delta, int64_t b, in
 
 template <int KERN, int KD, int C>
 cudaError_t launch_tc_inst(const TcParams& p, int grid, cudaStream_t st) {
-    constexpr size_t xa = 2u * 128 * KD * 2u, xb = 2u * 64 * KD * 2u, dt = 2u * C * 64 * 2u;
+    constexpr size_t xa = 2u * tc::kRows * KD * 2u, xb = 2u * tc::kChunk * KD * 2u, dt = 2u * C * tc::kChunk * 2u;
     const size_t smem = 2 * xa + tc::kStages * (xb + dt) + 1024;
     auto fn = kmv_tc_kernel<KERN, KD, C>;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -664,9 +726,11 @@ cudaError_t launch_tc_inst(const TcParams& p, int grid, cudaStream_t st) {
 
 int tc_kd(int d) { return d + 2 <= 16 ? 16 : 32; }
 
+int tc_chunks_per_block(int64_t b) { return (int)((b + tc::kChunk - 1) / tc::kChunk); }
+
 size_t tc_rows_bytes(int64_t ntiles, int kd) { return (size_t)ntiles * 2 * 128 * kd * 2; }
-size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * 2 * 64 * kd * 2; }
-size_t tc_delta_bytes(int cpb, int C) { return (size_t)cpb * 2 * C * 64 * 2; }
+size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * 2 * tc::kChunk * kd * 2; }
+size_t tc_delta_bytes(int cpb, int C) { return (size_t)cpb * 2 * C * tc::kChunk * 2; }
 
 cudaError_t launch_tc_pack_inputs(int kernel, const float* Xs, int64_t n, int d, int D, int64_t b, int64_t m,
                                   int64_t tps, int cpb, int kd, uint8_t* XA, uint8_t* XB, cudaStream_t st) {

@@ -63,10 +63,11 @@ size_t estimate_bytes(const ap_request& r) {
     bytes += (size_t)(m * ntri) * 64 * 64 * 4;                     // L^-1 cache
     bytes += (size_t)(4 * n * Cp) * 4 + (size_t)(nt * 64 + b) * Cp * 4;  // R, W, Bp, Tmp, Z, Delta
     if (r.precision != AP_FP32) {
-        const int64_t kd = d + 2 <= 16 ? 16 : 32;
-        bytes += (size_t)(m * ((b + 127) / 128)) * 2 * 128 * kd * 2;  // row operands
-        bytes += (size_t)(m * ((b + 63) / 64)) * 2 * 64 * kd * 2;     // column operands
-        bytes += (size_t)((b + 63) / 64) * 2 * 16 * 64 * 2;           // Delta^T
+        const int kd = ap::tc_kd((int)d);
+        const int cpb = ap::tc_chunks_per_block(b);
+        bytes += ap::tc_rows_bytes(m * ((b + 127) / 128), kd);  // row operands
+        bytes += ap::tc_cols_bytes(m, cpb, kd);                 // column operands
+        bytes += ap::tc_delta_bytes(cpb, 16);                   // Delta^T
     }
     bytes += (size_t)(M * D) * 4 + (size_t)(1 << 20);              // test inputs, partials
     const size_t ws_block = (size_t)(nt * 64) * (nt * 64) * 8 + (size_t)nt * 64 * 64 * 8;
