@@ -20,8 +20,9 @@
 // scheduler hide the SFU and tensor-memory latencies); warp 16 lane 0 issues
 // the distance MMAs, warp 17 lane 0 the contraction MMAs and warp 18 lane 0 the
 // bulk copies, so that no issuer waits behind another one's barriers.  The
-// three hi/lo products of the contraction accumulate into three separate
-// accumulators (independent MMA chains), summed in the epilogue.  S/P live in a
+// hi*hi and hi*lo products of the contraction are one MMA of width 2C (Delta_hi
+// and Delta_lo stacked), lo*hi a second one into its own accumulator; the three
+// partial sums are added in the epilogue.  S/P live in a
 // ring of three tensor-memory buffers (a buffer is reused once the contraction
 // that read its P has completed), operands in a ring of shared-memory stages;
 // everything is synchronised by mbarriers, and every wait is bounded in time
@@ -40,6 +41,8 @@ constexpr int kStages = 4;
 constexpr int kBufs = 3;     // S/P tensor-memory buffers
 constexpr int kXformWarps = 16;
 constexpr int kColsPerWarp = kChunk / (kXformWarps / 4);  // 32 columns of a chunk per warp
+constexpr int kUnits = kColsPerWarp / 16;                  // 16-column work units per warp and chunk
+constexpr int kGroups = kXformWarps / 4;                   // column groups of a chunk (4 warps each)
 constexpr int kLoadWarp = kXformWarps;       // distance MMAs (also owns the tensor memory)
 constexpr int kMmaWarp = kXformWarps + 1;    // contraction MMAs
 constexpr int kCopyWarp = kXformWarps + 2;   // bulk copies of the operand stages
@@ -295,9 +298,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     uint8_t* s_stage = tc_smem + 2 * kXaBytes;       // kStages buffers
     __shared__ __align__(8) uint64_t bar_stage_full[kStages], bar_stage_empty[kStages];
     __shared__ __align__(8) uint64_t bar_xa_full[2], bar_xa_empty[2];
-    // per S/P buffer: S written (distance MMAs), P written (transform warps),
-    // P consumed (contraction MMAs)
-    __shared__ __align__(8) uint64_t bar_s_full[kBufs], bar_p_full[kBufs], bar_buf_free[kBufs];
+    // per S/P buffer: S written (distance MMAs), P of one column group written
+    // (its four transform warps), P consumed (contraction MMAs)
+    __shared__ __align__(8) uint64_t bar_s_full[kBufs], bar_p_full[kBufs][kGroups], bar_buf_free[kBufs];
     __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_free;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         }
         for (int i = 0; i < kBufs; ++i) {
             mbar_init(&bar_s_full[i], 1);
-            mbar_init(&bar_p_full[i], kXformWarps);
+            for (int gq = 0; gq < kGroups; ++gq) mbar_init(&bar_p_full[i][gq], 4);
             mbar_init(&bar_buf_free[i], 1);
         }
         mbar_init(&bar_acc_full, 1);
@@ -418,33 +421,41 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ contraction MMA issuer
         if (lane == 0 && my_tiles > 0 && nq > 0) {
-            constexpr uint32_t idesc_c = instr_desc(1, kRows, C);  // BF16 x BF16 -> F32, 128 x C
+            // BF16 x BF16 -> F32: 128 x 2C (P_hi against [Delta_hi; Delta_lo]) and 128 x C
+            constexpr uint32_t idesc_c2 = instr_desc(1, kRows, 2 * C);
+            constexpr uint32_t idesc_c = instr_desc(1, kRows, C);
             bool ok = true;
             int64_t g = 0;
             for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
                 for (int q = 0; q < nq && ok; ++q, ++g) {
                     const int buf = (int)(g % kBufs);
                     const int s = (int)(g % kStages);
-                    ok = mbar_wait(&bar_p_full[buf], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
-                    if (ok && q == 0 && tt >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((tt - 1) & 1), &s_abort, p.err);
+                    if (q == 0 && tt >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((tt - 1) & 1), &s_abort, p.err);
                     if (!ok) break;
-                    tc_fence_after();
+                    // Delta^T of the stage: C rows of Delta_hi, then C rows of Delta_lo
+                    // (consecutive 8-row groups), so one N = 2C product gives hi*hi
+                    // and hi*lo side by side in accumulator columns [0, 2C)
                     const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
-                    const uint32_t dtl = dth + kDtBytes / 2;
                     const uint32_t pb = tmem + (uint32_t)(kChunk * buf);
-                    const uint32_t a0 = tmem + kColAcc, a1 = a0 + C, a2 = a0 + 2 * C;
+                    const uint32_t a01 = tmem + kColAcc, a2 = a01 + 2 * C;
                     // K-step ks: 16 BF16 values of P = 8 columns of P_hi at 16 ks and 8
                     // of P_lo at 16 ks + 8; two 16-byte core columns of Delta^T (core
-                    // columns 128 B apart)
+                    // columns 128 B apart).  The K-steps of a column group start as
+                    // soon as its four transform warps have written their P.
 #pragma unroll
                     for (int ks = 0; ks < KSTEPS_C; ++ks) {
+                        if (ks % kUnits == 0) {
+                            ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
+                            if (!ok) break;
+                            tc_fence_after();
+                        }
                         const uint32_t acc = (q == 0 && ks == 0) ? 0u : 1u;
                         const uint32_t boff = ks * 256;
                         const uint32_t pH = pb + 16u * ks, pL = pH + 8u;
-                        mma_ts(a0, pH, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
-                        mma_ts(a1, pH, smem_desc(dtl + boff, 128, kSboD), idesc_c, acc);
+                        mma_ts(a01, pH, smem_desc(dth + boff, 128, kSboD), idesc_c2, acc);
                         mma_ts(a2, pL, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
                     }
+                    if (!ok) break;
                     tc_commit(&bar_buf_free[buf]);
                     tc_commit(&bar_stage_empty[s]);
                     if (q == nq - 1) tc_commit(&bar_acc_full);
@@ -461,7 +472,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         const int total = (int)(my_tiles * nq);  // chunks of this CTA (< 2^31)
         bool ok = total > 0;
         uint32_t ta[16], tb[16];
-        // columns of unit (chunk c, half h): S there is replaced by [P_hi | P_lo]
+        // columns of unit (chunk c, unit h of this warp): S there is replaced by [P_hi | P_lo]
         auto u_addr = [&](int c, int h) -> uint32_t {
             return tmem + lane_base + (uint32_t)(kChunk * (c % kBufs) + kColsPerWarp * group + 16 * h);
         };
@@ -532,12 +543,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         int q_in_tile = 0;  // chunk index within the current tile
         int64_t tile_no = 0;
         // one unit: S of (c, h) is in `cur` (load issued); prefetch the next unit
-        // into `nxt`, transform, store P in place; after the second half of a chunk
+        // into `nxt`, transform, store P in place; after the last unit of a chunk
         // signal the contraction MMA
         auto unit = [&](int c, int h, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
             tmem_wait_ld();
-            if (h == 0) {
-                if (ok) tmem_ld16(u_addr(c, 1), nxt);
+            if (h + 1 < kUnits) {
+                if (ok) tmem_ld16(u_addr(c, h + 1), nxt);
             } else if (c + 1 < total) {
                 if (ok)
                     ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[(c + 1) % kBufs],
@@ -557,13 +568,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 pw[8 + k] = pack_bf16(lo.x, lo.y);
             }
             if (ok) tmem_st16(u_addr(c, h), pw);
-            if (h == 1) {
+            if (h == kUnits - 1) {
                 if (ok) {
                     tmem_wait_st();
                     tc_fence_before();
                 }
                 __syncwarp();
-                if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs]);
+                if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs][group]);
                 if (++q_in_tile == nq) {
                     if (warp < 4) epilogue(tile_no);
                     q_in_tile = 0;
@@ -580,9 +591,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         }
         // every chunk is visited even after a failed wait (without touching tensor
         // memory), so warps 0-3 make the same number of epilogue calls
-        for (int c = 0; c < total; ++c) {
-            unit(c, 0, ta, tb);
-            unit(c, 1, tb, ta);
+        const int total_units = total * kUnits;
+        for (int u = 0; u < total_units; u += 2) {
+            unit(u / kUnits, u % kUnits, ta, tb);
+            if (u + 1 < total_units) unit((u + 1) / kUnits, (u + 1) % kUnits, tb, ta);
         }
         tmem_wait_ld();
     }
