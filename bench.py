@@ -261,6 +261,9 @@ def run_ours(args, rank: int, world: int):
     ttt = None
     if rank == 0 and not args.no_ttt:
         ttt = time_to_tol_small(ap, torch, dev, stream)
+    mll = None
+    if rank == 0 and not args.no_mll:
+        mll = mll_grad_timing(ap, torch, dev, stream)
 
     if rank != 0:
         if dist:
@@ -268,6 +271,7 @@ def run_ours(args, rank: int, world: int):
         return
     line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt)
     line["other_forms"] = compare
+    line["mll_grad"] = mll
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, infos[-1]["epochs"], args)
     print(json.dumps(line), flush=True)
@@ -323,6 +327,39 @@ def time_to_tol_small(ap, torch, dev, stream) -> dict:
             "rel_res_true": i["rel_res_true"][0], "status": ap.ap_status_str(st)}
 
 
+def mll_grad_timing(ap, torch, dev, stream) -> dict:
+    """One stochastic MLL gradient (Eq. loss_grad_unbiased) on n = 131,072,
+    d = 8, Matern-3/2 ARD, noise 0.05, 31 Rademacher probes, blocks of 4096:
+    cache + AP solve of the 32 right-hand sides to the paper's training
+    tolerance (mean relative residual < 1, at least 11 epochs) in the
+    tensor-core form + the fused derivative quadratic forms.  Median of 3."""
+    p = wl.matern32_grad()
+    X = torch.from_numpy(p.X).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    Z = torch.from_numpy(np.ascontiguousarray(p.B[:, 1:])).to(dev)
+    hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+    times, infos, grads = [], [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = ap.ap_create(X, hyper, ap.ap_opts_default(block=p.block, tol=p.tol, stop=ap.AP_STOP_MEAN_REL,
+                                                        min_epochs=11, max_epochs=1000,
+                                                        precision=ap.AP_BF16_REFINE, refine_every=10,
+                                                        stream=stream.cuda_stream))
+        st, g, info = ap.ap_mll_grad(ctx, y, p.c - 1, Z)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        infos.append(info)
+        grads.append(g)
+        ap.ap_destroy(ctx)
+    i = infos[-1]
+    return {"workload": f"{p.name}: Matern-3/2 ARD, n={p.n}, d={p.d}, b={p.block}, 31 probes, noise={p.noise:g}, "
+                        "training tolerance 1 (mean rule, >= 11 epochs), BF16+refine solve",
+            "time_s": statistics.median(times), "cache_s": i["t_cache_s"], "solve_s": i["t_solve_s"],
+            "epochs": i["epochs"], "status": ap.ap_status_str(st),
+            "grad_norm": float(np.linalg.norm(grads[-1].astype(np.float64)))}
+
+
 def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt) -> dict:
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -330,7 +367,9 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
     n_up = max(1, last["n_update"])
     t_launch = last["t_update_s"] / n_up
     units = float(p.n) * float(p.block)
-    roof = roofline(p, args, t_launch, units, sm_max)
+    sfu = ap.ap_sfu_rates() if args.precision != "fp32" else (32.0, 16.0)
+    roof = roofline(p, args, t_launch, units, sm_max, sfu)
+    roof["sfu_rates_per_clk_sm"] = {"exp2": sfu[0], "sqrt": sfu[1]} if args.precision != "fp32" else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -370,10 +409,9 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
 # MUFU results per clock per SM on GB300.  ncu's pct-of-peak for the XU pipe
 # (28 % at 7.75 results/clk/SM measured on the tensor-core update kernel) puts
 # the pipe's peak at ~32/clk/SM (Blackwell Ultra doubled the SFU rate).
-SFU_OPS_PER_SM = 32
 
 
-def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
+def roofline(p, args, t_launch: float, units: float, sm_max: float, sfu=(32.0, 16.0)) -> dict:
     """Roofline of the dominant kernel (the fused residual update of one AP step)."""
     if args.precision == "fp32":
         flops_per_entry = 2 * p.c + 3 * p.d
@@ -386,9 +424,19 @@ def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
                 "per_unit": f"{flops_per_entry} FP32 flop per kernel entry (2c contraction + 3d distance)",
                 "peak_note": f"FP32 FMA pipe: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                              f"{sm_max:.0f} MHz (derived from unit counts and max clock)"}
-    mufu = 1 if p.kernel == wl.RBF else 2
-    achieved = units * mufu / t_launch / 1e12 if t_launch > 0 else None
-    peak = NUM_SMS * SFU_OPS_PER_SM * sm_max * 1e6 / 1e12
+    # SFU operations per entry: exp2 for every kernel, sqrt for the Matern ones.
+    # Peak: the measured per-clock rates of this GPU (ap_sfu_rates) at the
+    # maximum SM clock; for the Matern mix (one of each per entry) the pipe
+    # completes 2 / (1/r_exp2 + 1/r_sqrt) operations per clock and SM.
+    r_ex2, r_sqrt = sfu
+    if p.kernel == wl.RBF:
+        ops, per_clk = 1, r_ex2
+        mix = f"exp2 {r_ex2:.1f}/clk/SM"
+    else:
+        ops, per_clk = 2, 2.0 / (1.0 / r_ex2 + 1.0 / r_sqrt)
+        mix = f"1:1 exp2 ({r_ex2:.1f}/clk/SM) + sqrt ({r_sqrt:.1f}/clk/SM) = {per_clk:.2f}/clk/SM"
+    achieved = units * ops / t_launch / 1e12 if t_launch > 0 else None
+    peak = NUM_SMS * per_clk * sm_max * 1e6 / 1e12
     kd = 16 if p.d + 2 <= 16 else 32
     cp = max(16, p.c)
     # distance: three FP16 hi/lo products of K = kd; contraction: three BF16 hi/lo
@@ -398,9 +446,9 @@ def roofline(p, args, t_launch: float, units: float, sm_max: float) -> dict:
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic_from_profiles("kmv_tc_update", args.workload, args.precision, units),
             "kernel": "kmv_tc_kernel (tcgen05 fused residual update, one AP step)",
-            "per_unit": f"{mufu} SFU (MUFU) op per kernel entry; units are tera-ops/s of the SFU pipe",
-            "peak_note": f"SFU pipe: {NUM_SMS} SMs x {SFU_OPS_PER_SM} results/clk x {sm_max:.0f} MHz "
-                         "(derived from unit counts and max clock)",
+            "per_unit": f"{ops} SFU op(s) per kernel entry; units are tera-ops/s of the SFU pipe",
+            "peak_note": f"SFU pipe measured on this GPU by ap_sfu_rates: {mix}, x {NUM_SMS} SMs x "
+                         f"{sm_max:.0f} MHz",
             "tensor_tflops": units * tensor_flops / t_launch / 1e12 if t_launch > 0 else None,
             "tensor_flops_per_entry": tensor_flops}
 
@@ -524,6 +572,7 @@ def main():
     ap_.add_argument("--no-cpu-baseline", action="store_true")
     ap_.add_argument("--no-e2e", action="store_true")
     ap_.add_argument("--no-ttt", action="store_true")
+    ap_.add_argument("--no-mll", action="store_true", help="skip the MLL-gradient timing")
     ap_.add_argument("--serve", action="store_true", help="replay the serving workload instead")
     ap_.add_argument("--serve-requests", type=int, default=512)
     ap_.add_argument("--serve-rate", type=float, default=40.0)

@@ -235,6 +235,16 @@ ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const f
 /* Number of kernels this context has launched since ap_create (all calls). */
 int64_t ap_launch_count(const ap_ctx* ctx);
 
+/* Measured SFU throughput of the current device, in results per SM clock, of
+ * the two operations kernel evaluation is made of: ex2.approx (every kernel)
+ * and sqrt.approx (Matern kernels).  No counterpart in the paper; the
+ * benchmark divides by these rates to place the tensor-core residual update
+ * (bound by them) on its roofline.  Runs two probe kernels of about a
+ * millisecond on the current device and allocates ~1 MB there while it runs.
+ * Both pointers are host doubles.  AP_ERR_INVALID_ARG on NULL, AP_ERR_NOMEM /
+ * AP_ERR_CUDA on device errors. */
+ap_status ap_sfu_rates(double* ex2_per_clk_sm, double* sqrt_per_clk_sm);
+
 /* ------------------------------------------------------------------ serving
  * Continuous batching of GP solve + posterior-mean requests (no counterpart in
  * the paper, which solves one system at a time): requests are admitted in

@@ -27,7 +27,7 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_IN
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
+           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
 
 
 class ApError(RuntimeError):
@@ -217,6 +217,15 @@ def ap_mll_grad(ctx: Context, y, n_probes: int, Z=None):
 
 def ap_launch_count(ctx: Context) -> int:
     return int(_capi.load().ap_launch_count(ctx.handle))
+
+
+def ap_sfu_rates() -> tuple:
+    """(exp2, sqrt) SFU results per SM clock, measured on the current device."""
+    e, q = ctypes.c_double(), ctypes.c_double()
+    st = _capi.load().ap_sfu_rates(ctypes.byref(e), ctypes.byref(q))
+    if st != AP_OK:
+        raise ApError(st, "ap_sfu_rates")
+    return e.value, q.value
 
 
 def ap_destroy(ctx: Context) -> None:

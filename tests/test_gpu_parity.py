@@ -219,3 +219,10 @@ def test_warm_start_resumes():
     assert st == ap.AP_OK
     R = oracle.residual_rows(oracle.Hyper.of(p), _f64(p.X), _f64(p.B), _f64(W.cpu().numpy()))
     assert np.max(np.linalg.norm(R, axis=0) / np.linalg.norm(p.B, axis=0)) <= 2e-5
+
+
+def test_sfu_rates_are_plausible():
+    # per-SM-clock rates of the probe; exp2 runs at least as fast as sqrt on
+    # every NVIDIA part, and neither exceeds the 128 lanes of an SM
+    e, q = ap.ap_sfu_rates()
+    assert 4.0 <= q <= 1.05 * e <= 1.05 * 128.0, (e, q)
