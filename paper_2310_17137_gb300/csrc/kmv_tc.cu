@@ -2,9 +2,12 @@
 // with the Gauss-Southwell epilogue (Eq. approximate_gauss_southwell).
 //
 // Per 128-row tile of R and per 128-column chunk of the selected block I:
-//   1. S = [x_s | a | 1] [-2 x_s' | 1 | a']^T on the tensor cores, a = |x_s|^2, so
-//      S_ij = |x_s,i - x_s,j|^2 = t_ij directly (FP16 hi/lo operands, three
-//      products, FP32 accumulation in tensor memory);
+//   1. S_ij = |x_s,i - x_s,j|^2 = t_ij on the tensor cores as one product of
+//      [x_hi | x_hi | x_lo | a_hi | a_lo | 1 | 1] and
+//      [-2x'_hi | -2x'_lo | -2x'_hi | 1 | 1 | a'_hi | a'_lo] (a = |x_s|^2, every
+//      value split into an FP16 hi/lo pair; the three cross products of the
+//      pairs are laid out along K, so K = 3d + 4 rounded up to 16 and d <= 4
+//      needs a single MMA), FP32 accumulation in tensor memory;
 //   2. sixteen transform warps load t from tensor memory, evaluate phi on the
 //      SFU and write P = phi back as a BF16 hi/lo pair, in place: every 16
 //      FP32 columns of S become 8 columns of P_hi followed by 8 of P_lo;
@@ -50,6 +53,13 @@ constexpr int kThreads = (kXformWarps + 3) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = kBufs * kChunk;  // three accumulators (hi*hi, hi*lo, lo*hi), C columns each
 static_assert(kColAcc + 3 * 32 <= kTmemCols, "tensor memory budget");
+}  // namespace tc
+
+// K of the distance product for d <= 30 (the tensor-core forms' limit): 3d + 4
+// rounded up to 16; shared memory is sized for it at the largest d.
+constexpr int kTcMaxKdp = 96;
+
+namespace tc {
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------ PTX helpers
@@ -268,8 +278,9 @@ __device__ __forceinline__ float2 phi_tc2(float t0, float t1) {
 
 // -------------------------------------------------------------- kernel params
 struct TcParams {
-    const uint8_t* XA;     // row operand tiles: ntiles x (2 x 128 x KD fp16)
-    const uint8_t* XB;     // column operand chunks: m x cpb x (2 x 128 x KD fp16)
+    const uint8_t* XA;     // row operand tiles: ntiles x (128 x kdp fp16)
+    const uint8_t* XB;     // column operand chunks: m x cpb x (128 x kdp fp16)
+    int kdp;               // K of the distance product (multiple of 16)
     const uint8_t* DT;     // Delta^T chunks of this step: cpb x (2 x C x 128 bf16)
     const float* Delta;    // b x C FP32 (noise diagonal)
     float* R;              // n x C
@@ -281,17 +292,17 @@ struct TcParams {
     EpiParams epi;         // tiles of 128 rows aligned to blocks (tiles_per_seg = ceil(b / 128))
 };
 
-template <int KERN, int KD, int C>
+template <int KERN, int C>
 __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams p) {
     using namespace tc;
-    constexpr uint32_t kXaBytes = 2u * kRows * KD * 2u;   // hi + lo
-    constexpr uint32_t kXbBytes = 2u * kChunk * KD * 2u;  // hi + lo
+    const uint32_t kXaBytes = (uint32_t)(kRows * p.kdp * 2);
+    const uint32_t kXbBytes = (uint32_t)(kChunk * p.kdp * 2);
     constexpr uint32_t kDtBytes = 2u * C * kChunk * 2u;   // hi + lo
-    constexpr uint32_t kStageBytes = kXbBytes + kDtBytes;
-    constexpr int KSTEPS_D = KD / 16;
+    const uint32_t kStageBytes = kXbBytes + kDtBytes;
+    const int KSTEPS_D = p.kdp / 16;
     constexpr int KSTEPS_C = kChunk / 16;
-    constexpr uint32_t kSboX = (KD / 8) * 128;      // 8-row groups of the X operands
-    constexpr uint32_t kSboD = (kChunk / 8) * 128;  // 8-row groups of Delta^T
+    const uint32_t kSboX = (uint32_t)(p.kdp / 8) * 128;  // 8-row groups of the X operands
+    constexpr uint32_t kSboD = (kChunk / 8) * 128;       // 8-row groups of Delta^T
 
     extern __shared__ __align__(1024) uint8_t tc_smem[];
     uint8_t* s_xa = tc_smem;                         // 2 buffers
@@ -391,8 +402,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
                 const int xb = (int)(tt & 1);
                 ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((tt >> 1) & 1), &s_abort, p.err);
-                const uint32_t xa_hi = smem_u32(s_xa + (size_t)xb * kXaBytes);
-                const uint32_t xa_lo = xa_hi + kXaBytes / 2;
+                const uint32_t xa = smem_u32(s_xa + (size_t)xb * kXaBytes);
                 for (int q = 0; q < nq && ok; ++q, ++g) {
                     const int s = (int)(g % kStages);
                     const int buf = (int)(g % kBufs);
@@ -401,17 +411,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                     if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t xbh = smem_u32(s_stage + (size_t)s * kStageBytes);
-                    const uint32_t xbl = xbh + kXbBytes / 2;
+                    const uint32_t xbs = smem_u32(s_stage + (size_t)s * kStageBytes);
                     const uint32_t dS = tmem + (uint32_t)(kChunk * buf);
-                    uint32_t acc = 0;
-#pragma unroll
                     for (int ks = 0; ks < KSTEPS_D; ++ks) {
                         const uint32_t off = ks * 256;
-                        mma_ss(dS, smem_desc(xa_hi + off, 128, kSboX), smem_desc(xbh + off, 128, kSboX), idesc_d, acc);
-                        acc = 1;
-                        mma_ss(dS, smem_desc(xa_hi + off, 128, kSboX), smem_desc(xbl + off, 128, kSboX), idesc_d, 1);
-                        mma_ss(dS, smem_desc(xa_lo + off, 128, kSboX), smem_desc(xbh + off, 128, kSboX), idesc_d, 1);
+                        mma_ss(dS, smem_desc(xa + off, 128, kSboX), smem_desc(xbs + off, 128, kSboX), idesc_d,
+                               ks > 0 ? 1u : 0u);
                     }
                     tc_commit(&bar_s_full[buf]);
                     if (q == nq - 1) tc_commit(&bar_xa_empty[xb]);
@@ -639,67 +644,73 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
     lo = __float2half_rn(v - __half2float(hi));
 }
 
-// Row operand tiles: [x_s | a | 1 | 0...] for the rows of every block-aligned tile.
+// Value at K index k of the distance operand of a point with scaled (and
+// log2(e)-folded) coordinates z[0..d) and a = |z|^2.  Rows (the tile's points):
+// [z_hi | z_hi | z_lo | a_hi | a_lo | 1 | 1 | 0...]; columns (the block's
+// points): [-2z_hi | -2z_lo | -2z_hi | 1 | 1 | a_hi | a_lo | 0...], so that the
+// product of a row and a column sums the cross terms hi*hi + hi*lo + lo*hi and
+// both squared norms.
+__device__ __forceinline__ __half dist_operand(const double* z, double a, int d, int k, bool column) {
+    __half hi, lo;
+    if (k < 3 * d) {
+        const int q = k % d, part = k / d;  // part 0, 1, 2
+        split_f16((float)(column ? -2.0 * z[q] : z[q]), hi, lo);
+        if (column) return part == 1 ? lo : hi;
+        return part == 2 ? lo : hi;
+    }
+    const int r = k - 3 * d;
+    if (r >= 4) return __float2half_rn(0.0f);
+    split_f16((float)a, hi, lo);
+    if (!column) return r == 0 ? hi : r == 1 ? lo : __float2half_rn(1.0f);
+    return r < 2 ? __float2half_rn(1.0f) : (r == 2 ? hi : lo);
+}
+
+// Row operand tiles, for the rows of every block-aligned tile (zero rows past
+// the end of a block).
 __global__ void pack_rows_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int64_t tps,
-                                 int KD, float fold, uint8_t* __restrict__ XA) {
+                                 int kdp, float fold, uint8_t* __restrict__ XA) {
     const int64_t tile = blockIdx.x;
     const int64_t seg_lo = (tile / tps) * b;
     const int64_t seg_hi = min(seg_lo + b, n);
     const int64_t r0 = seg_lo + (tile % tps) * 128;
-    const size_t half_bytes = (size_t)128 * KD * 2;
-    uint8_t* dst = XA + (size_t)tile * 2 * half_bytes;
-    for (int t = threadIdx.x; t < 128 * KD; t += blockDim.x) {
-        const int row = t / KD, k = t % KD;
+    uint8_t* dst = XA + (size_t)tile * 128 * kdp * 2;
+    for (int t = threadIdx.x; t < 128 * kdp; t += blockDim.x) {
+        const int row = t / kdp, k = t % kdp;
         const int64_t i = r0 + row;
-        float v = 0.0f;
+        __half v = __float2half_rn(0.0f);
         if (i < seg_hi) {
-            if (k < d) {
-                v = (float)((double)Xs[i * D + k] * fold);
-            } else if (k == d) {
-                double a = 0.0;
-                for (int q = 0; q < d; ++q) a += (double)Xs[i * D + q] * (double)Xs[i * D + q];
-                v = (float)(a * fold * fold);
-            } else if (k == d + 1) {
-                v = 1.0f;
+            double z[AP_MAX_DIM], a = 0.0;
+            for (int q = 0; q < d; ++q) {
+                z[q] = (double)Xs[i * D + q] * fold;
+                a += z[q] * z[q];
             }
+            v = dist_operand(z, a, d, k, false);
         }
-        __half hi, lo;
-        split_f16(v, hi, lo);
-        const size_t off = core_off(row, k, KD);
-        *reinterpret_cast<__half*>(dst + off) = hi;
-        *reinterpret_cast<__half*>(dst + half_bytes + off) = lo;
+        *reinterpret_cast<__half*>(dst + core_off(row, k, kdp)) = v;
     }
 }
 
-// Column operand chunks: [-2 x_s | 1 | a | 0...] for 128 columns per chunk, per block.
-__global__ void pack_cols_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int cpb, int KD,
+// Column operand chunks: 128 columns per chunk, per block (zero past its end).
+__global__ void pack_cols_kernel(const float* __restrict__ Xs, int64_t n, int d, int D, int64_t b, int cpb, int kdp,
                                  float fold, uint8_t* __restrict__ XB) {
     const int64_t chunk = blockIdx.x;  // block * cpb + q
     const int64_t blk = chunk / cpb;
     const int q = (int)(chunk % cpb);
     const int64_t lo_col = blk * b, hi_col = min(lo_col + b, n);
-    const size_t half_bytes = (size_t)tc::kChunk * KD * 2;
-    uint8_t* dst = XB + (size_t)chunk * 2 * half_bytes;
-    for (int t = threadIdx.x; t < tc::kChunk * KD; t += blockDim.x) {
-        const int row = t / KD, k = t % KD;
+    uint8_t* dst = XB + (size_t)chunk * tc::kChunk * kdp * 2;
+    for (int t = threadIdx.x; t < tc::kChunk * kdp; t += blockDim.x) {
+        const int row = t / kdp, k = t % kdp;
         const int64_t j = lo_col + (int64_t)q * tc::kChunk + row;
-        float v = 0.0f;
+        __half v = __float2half_rn(0.0f);
         if (j < hi_col) {
-            if (k < d) {
-                v = (float)(-2.0 * (double)Xs[j * D + k] * fold);
-            } else if (k == d) {
-                v = 1.0f;
-            } else if (k == d + 1) {
-                double a = 0.0;
-                for (int s = 0; s < d; ++s) a += (double)Xs[j * D + s] * (double)Xs[j * D + s];
-                v = (float)(a * fold * fold);
+            double z[AP_MAX_DIM], a = 0.0;
+            for (int s = 0; s < d; ++s) {
+                z[s] = (double)Xs[j * D + s] * fold;
+                a += z[s] * z[s];
             }
+            v = dist_operand(z, a, d, k, true);
         }
-        __half hi, lo;
-        split_f16(v, hi, lo);
-        const size_t off = core_off(row, k, KD);
-        *reinterpret_cast<__half*>(dst + off) = hi;
-        *reinterpret_cast<__half*>(dst + half_bytes + off) = lo;
+        *reinterpret_cast<__half*>(dst + core_off(row, k, kdp)) = v;
     }
 }
 
@@ -723,11 +734,12 @@ __global__ void pack_delta_kernel(const float* __restrict__ Delta, int64_t b, in
     }
 }
 
-template <int KERN, int KD, int C>
+template <int KERN, int C>
 cudaError_t launch_tc_inst(const TcParams& p, int grid, cudaStream_t st) {
-    constexpr size_t xa = 2u * tc::kRows * KD * 2u, xb = 2u * tc::kChunk * KD * 2u, dt = 2u * C * tc::kChunk * 2u;
+    const size_t xa = (size_t)tc::kRows * p.kdp * 2, xb = (size_t)tc::kChunk * p.kdp * 2;
+    constexpr size_t dt = 2u * C * tc::kChunk * 2u;
     const size_t smem = 2 * xa + tc::kStages * (xb + dt) + 1024;
-    auto fn = kmv_tc_kernel<KERN, KD, C>;
+    auto fn = kmv_tc_kernel<KERN, C>;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     fn<<<grid, tc::kThreads, smem, st>>>(p);
@@ -736,12 +748,12 @@ cudaError_t launch_tc_inst(const TcParams& p, int grid, cudaStream_t st) {
 
 }  // namespace
 
-int tc_kd(int d) { return d + 2 <= 16 ? 16 : 32; }
+int tc_kd(int d) { return (3 * d + 4 + 15) / 16 * 16; }
 
 int tc_chunks_per_block(int64_t b) { return (int)((b + tc::kChunk - 1) / tc::kChunk); }
 
-size_t tc_rows_bytes(int64_t ntiles, int kd) { return (size_t)ntiles * 2 * 128 * kd * 2; }
-size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * 2 * tc::kChunk * kd * 2; }
+size_t tc_rows_bytes(int64_t ntiles, int kd) { return (size_t)ntiles * 128 * kd * 2; }
+size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * tc::kChunk * kd * 2; }
 size_t tc_delta_bytes(int cpb, int C) { return (size_t)cpb * 2 * C * tc::kChunk * 2; }
 
 cudaError_t launch_tc_pack_inputs(int kernel, const float* Xs, int64_t n, int d, int D, int64_t b, int64_t m,
@@ -759,12 +771,11 @@ cudaError_t launch_tc_pack_delta(const float* Delta, int64_t b, int C, int cpb, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_kmv_tc(int kernel, const TcParams& p, int kd, int C, int grid, cudaStream_t st) {
-#define AP_TC_K(KK)                                                         \
-    if (kd == 16 && C == 16) return launch_tc_inst<KK, 16, 16>(p, grid, st); \
-    if (kd == 16 && C == 32) return launch_tc_inst<KK, 16, 32>(p, grid, st); \
-    if (kd == 32 && C == 16) return launch_tc_inst<KK, 32, 16>(p, grid, st); \
-    if (kd == 32 && C == 32) return launch_tc_inst<KK, 32, 32>(p, grid, st); \
+cudaError_t launch_kmv_tc(int kernel, const TcParams& p, int C, int grid, cudaStream_t st) {
+    if (p.kdp < 16 || p.kdp % 16 != 0 || p.kdp > kTcMaxKdp) return cudaErrorInvalidValue;
+#define AP_TC_K(KK)                                                 \
+    if (C == 16) return launch_tc_inst<KK, 16>(p, grid, st); \
+    if (C == 32) return launch_tc_inst<KK, 32>(p, grid, st); \
     return cudaErrorInvalidValue;
     switch (kernel) {
         case AP_RBF: { AP_TC_K(AP_RBF) }
@@ -785,12 +796,13 @@ cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int
     p.n = l.n;
     p.b = l.b;
     p.cpb = l.cpb;
+    p.kdp = kd;
     p.s = l.s;
     p.noise = l.noise;
     p.sel = l.sel;
     p.err = l.err;
     p.epi = l.epi;
-    return launch_kmv_tc(kernel, p, kd, C, grid, st);
+    return launch_kmv_tc(kernel, p, C, grid, st);
 }
 
 }  // namespace ap
