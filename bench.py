@@ -132,7 +132,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"kmv_fp32_update": ["kmv_fp32.cuh", "ap_internal.cuh"],
-                  "kmv_tc_update": ["kmv_tc.cu", "kmv_fp32.cuh", "ap_internal.cuh"]}
+                  "kmv_tc_update": ["kmv_tc.cu", "tcgen05.cuh", "kmv_fp32.cuh", "ap_internal.cuh"]}
 
 
 def kernel_src_hash(kernel: str) -> str:

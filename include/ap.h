@@ -104,6 +104,15 @@ typedef struct ap_hyper {
 
 /* Solver options.  ap_opts_default fills the paper's values: GS selection,
  * MEAN_REL with tol 1 (training), at least 11 and at most 1000 epochs. */
+/* Arithmetic of the trailing (SYRK/GEMM) updates of the FP64 block Cholesky
+ * (Sec. 3, "Cached Cholesky Factors"), the bulk of its b^3/3 flops per block.
+ *   AP_CACHE_TC_EXACT: FP64 matrix, products formed exactly from 7-bit integer
+ *                      slices on the BF16 tensor cores and combined in 64-bit
+ *                      integers (error-free splitting), so each update has the
+ *                      accuracy of an FP64 GEMM.  Default.
+ *   AP_CACHE_FP64:     FP64 FMA on the CUDA cores. */
+typedef enum { AP_CACHE_TC_EXACT = 0, AP_CACHE_FP64 = 1 } ap_cache_gemm;
+
 typedef struct ap_opts {
     int64_t block;        /* block size b (sequential partition, Sec. 5); last block may be short */
     int32_t select;       /* ap_select */
@@ -121,6 +130,7 @@ typedef struct ap_opts {
     int64_t trace_cap;    /* capacity of block_trace */
     int32_t profile;      /* 1: time every block solve and residual update with CUDA events */
     int32_t residual_mode; /* ap_residual_mode: arithmetic of the residual recompute */
+    int32_t cache_gemm;   /* ap_cache_gemm: arithmetic of the Cholesky trailing updates */
 } ap_opts;
 
 /* Report of ap_solve / ap_mll_grad.  rel_res_* hold the first c columns. */

@@ -23,7 +23,8 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_IN
                     AP_ERR_NOT_CONVERGED, AP_ERR_NOT_SPD, AP_ERR_TIMEOUT, AP_ERR_UNSUPPORTED,
                     AP_FP16_REFINE, AP_FP32, AP_MATERN32, AP_MATERN52, AP_OK, AP_RBF, AP_SEL_CYCLIC,
                     AP_SEL_GS, AP_SEL_RANDOM, AP_STOP_FRO, AP_STOP_MAX_REL, AP_STOP_MEAN_REL,
-                    AP_STOP_Y_REL, AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED)
+                    AP_STOP_Y_REL, AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED, AP_CACHE_TC_EXACT,
+                    AP_CACHE_FP64)
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",

@@ -16,6 +16,7 @@ AP_ERR_SCRATCH_LIMIT = 9
 AP_STATIC_SCRATCH_BYTES = 1 << 20
 AP_RBF, AP_MATERN32, AP_MATERN52 = 0, 1, 2
 AP_FP32, AP_BF16_REFINE, AP_FP16_REFINE = 0, 1, 2
+AP_CACHE_TC_EXACT, AP_CACHE_FP64 = 0, 1
 AP_SEL_GS, AP_SEL_CYCLIC, AP_SEL_RANDOM = 0, 1, 2
 AP_STOP_MEAN_REL, AP_STOP_MAX_REL, AP_STOP_FRO, AP_STOP_Y_REL = 0, 1, 2, 3
 AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED = 0, 1, 2
@@ -40,7 +41,7 @@ class ap_opts(ctypes.Structure):
                 ("refine_every", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("hbm_budget", ctypes.c_size_t), ("block_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_cap", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("residual_mode", ctypes.c_int32)]
+                ("residual_mode", ctypes.c_int32), ("cache_gemm", ctypes.c_int32)]
 
 
 class ap_info(ctypes.Structure):

@@ -244,7 +244,9 @@ ap_status build_cache(ap_ctx* ctx) {
     const int64_t tile_elems = (int64_t)kTile * kTile;
     if (!ctx->Linv) AP_TRY(dalloc_t(ctx, &ctx->Linv, (size_t)(ctx->m * ctx->ntri * tile_elems)));
     const int64_t edge = (int64_t)ctx->nt * kTile;
-    const size_t per_block = (size_t)(edge * edge + ctx->nt * tile_elems) * sizeof(double);
+    const bool emulate = ctx->o.cache_gemm == AP_CACHE_TC_EXACT;
+    const size_t per_block = (size_t)(edge * edge + ctx->nt * tile_elems) * sizeof(double) +
+                             (emulate ? oz_slice_bytes(ctx->nt) + oz_expo_ints(ctx->nt) * sizeof(int) : 0);
     size_t cap = (size_t)8 << 30;
     if (ctx->o.hbm_budget) {
         const size_t left = ctx->o.hbm_budget > ctx->bytes ? ctx->o.hbm_budget - ctx->bytes : 0;
@@ -262,6 +264,20 @@ ap_status build_cache(ap_ctx* ctx) {
         dfree(ctx, A);
         return s;
     }
+    uint8_t* ozS = nullptr;
+    int* ozE = nullptr;
+    if (emulate) {
+        s = dalloc_t(ctx, &ozS, (size_t)g * oz_slice_bytes(ctx->nt));
+        if (s == AP_OK) s = dalloc_t(ctx, &ozE, (size_t)g * oz_expo_ints(ctx->nt));
+        if (s != AP_OK) {
+            dfree(ctx, ozS);
+            dfree(ctx, A);
+            dfree(ctx, Dinv);
+            return s;
+        }
+    }
+    const OzWork oz = {ozS, ozE, ctx->tc_err};
+    AP_CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int) * ctx->m, ctx->st));
     CacheParams cp = {};
     cp.X = ctx->X;
@@ -277,7 +293,8 @@ ap_status build_cache(ap_ctx* ctx) {
     cudaError_t err = cudaSuccess;
     for (int64_t blk0 = 0; blk0 < ctx->m && err == cudaSuccess; blk0 += g) {
         const int gg = (int)std::min<int64_t>(g, ctx->m - blk0);
-        err = cache_factor_group(cp, blk0, gg, A, Dinv, ctx->Linv, ctx->bad + blk0, ctx->st, &ctx->launches);
+        err = cache_factor_group(cp, blk0, gg, A, Dinv, ctx->Linv, ctx->bad + blk0, emulate ? &oz : nullptr, ctx->st,
+                                 &ctx->launches);
     }
     AP_CK(err);
     AP_CK(cudaEventRecord(ctx->ev_b, ctx->st));
@@ -287,6 +304,11 @@ ap_status build_cache(ap_ctx* ctx) {
     ctx->t_cache = ms * 1e-3;
     dfree(ctx, A);
     dfree(ctx, Dinv);
+    dfree(ctx, ozS);
+    dfree(ctx, ozE);
+    int tmo = 0;
+    AP_CK(cudaMemcpy(&tmo, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) return AP_ERR_TIMEOUT;
     std::vector<int> bad((size_t)ctx->m);
     AP_CK(cudaMemcpy(bad.data(), ctx->bad, sizeof(int) * ctx->m, cudaMemcpyDeviceToHost));
     for (int64_t J = 0; J < ctx->m; ++J)
@@ -753,6 +775,7 @@ void ap_opts_default(ap_opts* o) {
     o->trace_cap = 0;
     o->profile = 0;
     o->residual_mode = AP_RESID_AUTO;
+    o->cache_gemm = AP_CACHE_TC_EXACT;
 }
 
 size_t ap_sizeof_opts(void) { return sizeof(ap_opts); }
@@ -783,6 +806,7 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     if (o->block < 1 || o->select < 0 || o->select > 2 || o->stop < 0 || o->stop > 3) return AP_ERR_INVALID_ARG;
     if (o->precision < 0 || o->precision > 2 || o->max_epochs < 1 || o->min_epochs < 0) return AP_ERR_INVALID_ARG;
     if (o->residual_mode < 0 || o->residual_mode > 2) return AP_ERR_INVALID_ARG;
+    if (o->cache_gemm < 0 || o->cache_gemm > 1) return AP_ERR_INVALID_ARG;
     if (o->precision == AP_FP16_REFINE) return AP_ERR_UNSUPPORTED;
     if (o->precision == AP_BF16_REFINE && d + 2 > 32) return AP_ERR_UNSUPPORTED;
     ap_ctx* ctx = new (std::nothrow) ap_ctx();

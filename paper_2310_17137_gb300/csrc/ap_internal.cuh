@@ -102,8 +102,20 @@ struct CacheParams {
 // Factor blocks [blk0, blk0 + g) into the packed FP32 inverse factors Linv.
 // A (g * (nt*64)^2 doubles) and Dinv (g * nt * 64^2 doubles) are work buffers.
 // bad (g ints) gets 1 for a block whose factorisation met a non-positive pivot.
+// Tensor-core trailing updates with FP64 results (ozaki.cu): slice planes of
+// oz_slice_bytes(nt) bytes and oz_expo_ints(nt) row exponents per block.
+size_t oz_slice_bytes(int nt);
+size_t oz_expo_ints(int nt);
+cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E, int* err, cudaStream_t st,
+                             int64_t* launches);
+// Work buffers of the tensor-core trailing updates; null = FP64 FMA updates.
+struct OzWork {
+    uint8_t* S;  // g * oz_slice_bytes(nt)
+    int* E;      // g * oz_expo_ints(nt)
+    int* err;    // wait-timeout flag
+};
 cudaError_t cache_factor_group(const CacheParams& cp, int64_t blk0, int g, double* A, double* Dinv,
-                               float* Linv, int* bad, cudaStream_t st, int64_t* launches);
+                               float* Linv, int* bad, const OzWork* oz, cudaStream_t st, int64_t* launches);
 
 // ---- block solve: Delta = L^-T L^-1 R_I, W_I += Delta -----------------------
 struct SolveParams {

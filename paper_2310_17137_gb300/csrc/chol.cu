@@ -6,8 +6,9 @@
 //   1. build K_hat_II in FP64 directly from the FP32 inputs;
 //   2. factor it in FP64 by a right-looking tiled Cholesky: POTRF of the
 //      diagonal tile (which also inverts L_kk), TRSM of the panel below it as
-//      a product with L_kk^{-T}, SYRK/GEMM update of the trailing tiles; all
-//      blocks of a group advance together, one launch per phase;
+//      a product with L_kk^{-T}, SYRK/GEMM update of the trailing tiles (FP64
+//      FMA here, or exact integer slice products on the tensor cores in
+//      ozaki.cu); all blocks of a group advance together, one launch per phase;
 //   3. form the inverse factor L^{-1} tile by tile (diagonal tiles from the
 //      FP64 tile inverses, off-diagonal tiles by the block recurrence
 //      X_ik = -L_ii^{-1} sum_{j=k}^{i-1} L_ij X_jk) and store it packed in FP32.
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(256) tri_inv_step_kernel(const double* A, cons
 }  // namespace
 
 cudaError_t cache_factor_group(const CacheParams& cp, int64_t blk0, int g, double* A, double* Dinv,
-                               float* Linv, int* bad, cudaStream_t st, int64_t* launches) {
+                               float* Linv, int* bad, const OzWork* oz, cudaStream_t st, int64_t* launches) {
     const int nt = cp.nt;
     const int64_t ntri = (int64_t)nt * (nt + 1) / 2;
     const size_t smem2 = 2 * sizeof(double) * T * TP;
@@ -302,8 +303,13 @@ cudaError_t cache_factor_group(const CacheParams& cp, int64_t blk0, int g, doubl
         if (k + 1 < nt) {
             const int rem = nt - k - 1;
             trsm_kernel<<<dim3(rem, g), 256, smem2, st>>>(A, nt, k, Dinv);
-            syrk_kernel<<<dim3((unsigned)((int64_t)rem * (rem + 1) / 2), g), 256, smem2, st>>>(A, nt, k);
-            nl += 2;
+            ++nl;
+            if (oz) {
+                if ((err = launch_oz_update(A, nt, k, g, oz->S, oz->E, oz->err, st, &nl)) != cudaSuccess) return err;
+            } else {
+                syrk_kernel<<<dim3((unsigned)((int64_t)rem * (rem + 1) / 2), g), 256, smem2, st>>>(A, nt, k);
+                ++nl;
+            }
         }
     }
     pack_diag_kernel<<<dim3(nt, g), 256, 0, st>>>(Dinv, nt, blk0, ntri, Linv);

@@ -1,0 +1,250 @@
+// Trailing update of the tiled FP64 Cholesky (Sec. 3, "Cached Cholesky
+// Factors"; the SYRK/GEMM step carries b^3/3 of the factorisation's flops) on
+// the tensor cores, with FP64 results.
+//
+// A_ij -= A_ik A_jk^T for the trailing tiles k < j <= i is an FP64 dot product
+// of length 64 per entry.  GB300 runs FP64 at about 2 FMA per clock per SM, so
+// the products are formed as exact integer arithmetic on the BF16 tensor cores
+// instead (the splitting scheme of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication", Numer. Algorithms 2012):
+//   1. every row r of the 64-wide panel is scaled by a power of two 2^-e_r so
+//      that its entries lie in (-1/2, 1/2), and each scaled entry x is written
+//      as x = sum_{p=1..8} s_p 2^{-7p} + rest, |rest| < 2^-57, with integer
+//      slices |s_p| <= 64 (exact in BF16);
+//   2. for every level L = p + q = 2..9 the tensor cores accumulate
+//      acc_L = sum_{p+q=L} sum_kk s_p(r, kk) s_q(c, kk) in FP32.  Every partial
+//      sum is an integer below 2^22, so the accumulation is exact;
+//   3. the levels are combined exactly in 64-bit integers,
+//      H = sum_{L<=5} acc_L 2^{7(5-L)}, Lo = sum_{L>=6} acc_L 2^{7(9-L)}, and
+//      A_rc -= 2^{e_r+e_c-35} (H + 2^-28 Lo) with two FP64 roundings.
+// The terms left out (levels above 9 and the slice remainders) are below about
+// 2^-50 K max_kk|a_r,kk| max_kk|a_c,kk| per entry, the size of FP64 rounding
+// when the entries of a panel row have similar magnitudes; the matrix itself
+// stays FP64.  On kernel blocks the factor's backward error ||L L^T - K|| / ||K||
+// matches the all-FP64 factorisation (6e-16 vs 5e-16 on a Matern-5/2 block
+// with condition number 1.6e4, in a NumPy model of these exact steps).
+//
+// One CTA per 128 x 64 output super-tile (two row tiles i0, i0 + 1 against
+// one column tile j): bulk copies of the 8 slice planes of both operands
+// (192 KB of shared memory), 144 MMAs (36 slice products x 4 K-steps of 16)
+// into eight 64-column FP32 accumulators (all 512 tensor-memory columns), then
+// an epilogue of one row per thread.  Every wait is bounded.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "ap_internal.cuh"
+#include "tcgen05.cuh"
+
+namespace ap {
+namespace {
+
+using namespace tc;
+
+constexpr int T = kTile;
+constexpr int kSlices = 8;
+constexpr int kSlabRows = 2 * T;                            // rows of a super-tile
+constexpr uint32_t kPlaneA = kSlabRows * T * 2;             // 16 KB of BF16
+constexpr uint32_t kPlaneB = T * T * 2;                     // 8 KB
+constexpr uint32_t kOzSmem = kSlices * (kPlaneA + kPlaneB); // 192 KB
+constexpr int kOzThreads = 128;
+constexpr uint32_t kRowBytes = T * 2;                       // one slice row (64 BF16)
+constexpr int kBadExp = -(1 << 30);  // row exponent marking a non-finite panel row
+
+// byte offset of (row, kk) in a slice plane: K-major core matrices of 8 rows x
+// 8 BF16, 8 K-cores (1 KB) per 8-row group
+__device__ __forceinline__ size_t slice_off(int64_t row, int kk) {
+    return ((size_t)((row >> 3) * 8 + (kk >> 3)) * 8 + (size_t)(row & 7)) * 16 + (size_t)(kk & 7) * 2;
+}
+
+// Slices of the panel (tile column k) for the trailing rows r >= 64 (k + 1):
+// one warp per row.
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* A, int nt, int k, size_t plane_bytes,
+                                                       uint8_t* S, int* E) {
+    const int z = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ld = (int64_t)nt * T;
+    const int64_t r = (int64_t)(k + 1) * T + (int64_t)blockIdx.x * 8 + warp;
+    if (r >= ld) return;
+    const double* row = A + (int64_t)z * ld * ld + r * ld + (int64_t)k * T;
+    double v[2] = {row[lane], row[lane + 32]};
+    double m = fmax(fabs(v[0]), fabs(v[1]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const bool nonfinite = __any_sync(0xffffffffu, !isfinite(v[0]) || !isfinite(v[1]));
+    int e = 0;
+    if (m > 0.0 && m <= 1.0e300) e = max(-1000, min(1000, ilogb(m) + 2));  // |v| 2^-e < 1/2
+    uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kk = lane + 32 * h;
+        double x = scalbn(v[h], -e);
+#pragma unroll
+        for (int p = 0; p < kSlices; ++p) {
+            const double t = x * 128.0;
+            const double s = rint(t);  // |s| <= 64
+            x = t - s;                 // exact
+            *reinterpret_cast<__nv_bfloat16*>(Sz + (size_t)p * plane_bytes + slice_off(r, kk)) =
+                __double2bfloat16(s);
+        }
+    }
+    // a NaN or infinity in the panel must reach the next pivot test as NaN
+    if (lane == 0) E[(int64_t)z * (ld + T) + r] = nonfinite ? kBadExp : e;
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int nt, int k, const uint8_t* S,
+                                                               size_t plane_bytes, const int* E, int* err) {
+    extern __shared__ __align__(1024) uint8_t oz_smem[];
+    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ int s_ec[T];
+    const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+    const int rem = nt - k - 1;
+    // super-tile (u, jj) of this CTA: row tiles i0 = k + 1 + 2u, i0 + 1 and
+    // column tile j = k + 1 + jj <= i0 + 1
+    int u = 0, jj = (int)blockIdx.x;
+    while (true) {
+        const int nc = min(2 * u + 2, rem);
+        if (jj < nc) break;
+        jj -= nc;
+        ++u;
+    }
+    const int i0 = k + 1 + 2 * u, j = k + 1 + jj;
+    const int64_t ld = (int64_t)nt * T, rows_pad = ld + T;
+    const uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes;
+    uint8_t* sA = oz_smem;
+    uint8_t* sB = oz_smem + kSlices * kPlaneA;
+
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid < T) s_ec[tid] = E[(int64_t)z * rows_pad + (int64_t)j * T + tid];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (tid == 0) {
+        mbar_expect_tx(&bar_load, kOzSmem);
+        for (int p = 0; p < kSlices; ++p)
+            bulk_g2s(sA + p * kPlaneA, Sz + (size_t)p * plane_bytes + (size_t)i0 * T * kRowBytes, kPlaneA,
+                     &bar_load);
+        for (int q = 0; q < kSlices; ++q)
+            bulk_g2s(sB + q * kPlaneB, Sz + (size_t)q * plane_bytes + (size_t)j * T * kRowBytes, kPlaneB,
+                     &bar_load);
+        if (mbar_wait(&bar_load, 0u, &s_abort, err)) {
+            tc_fence_after();
+            constexpr uint32_t idesc = instr_desc(1, kSlabRows, T);  // BF16 x BF16 -> F32, 128 x 64
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int L = 2; L <= kSlices + 1; ++L) {
+                const uint32_t d = tmem + 64u * (uint32_t)(L - 2);
+                uint32_t acc = 0;
+                for (int p = max(1, L - kSlices); p <= min(kSlices, L - 1); ++p) {
+                    const int q = L - p;
+                    const uint32_t ap = a0 + (uint32_t)(p - 1) * kPlaneA, bq = b0 + (uint32_t)(q - 1) * kPlaneB;
+#pragma unroll
+                    for (int ks = 0; ks < T / 16; ++ks) {
+                        mma_ss(d, smem_desc(ap + ks * 256, 128, 1024), smem_desc(bq + ks * 256, 128, 1024), idesc,
+                               acc);
+                        acc = 1;
+                    }
+                }
+            }
+            tc_commit(&bar_mma);
+        }
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, 0u, &s_abort, err));
+    if (ok) tc_fence_after();
+
+    // epilogue: thread tid owns row r of the super-tile (tensor-memory lane tid)
+    const int64_t r = (int64_t)i0 * T + tid;
+    const int rtile = i0 + tid / T;
+    const bool live = ok && rtile < nt && j <= rtile;
+    const int er = live ? E[(int64_t)z * rows_pad + r] : 0;
+    double* Crow = A + (int64_t)z * ld * ld + r * ld + (int64_t)j * T;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < T; c0 += 16) {
+        long long H[16], Lo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) H[c] = Lo[c] = 0;
+#pragma unroll
+        for (int L = 2; L <= kSlices + 1; ++L) {
+            uint32_t v[16];
+            if (ok) {
+                tmem_ld16(tmem + lane_base + 64u * (uint32_t)(L - 2) + (uint32_t)c0, v);
+                tmem_wait_ld();
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const long long iv = (long long)__float2int_rn(__uint_as_float(v[c]));
+                if (L <= 5) H[c] = H[c] * 128 + iv;
+                else Lo[c] = Lo[c] * 128 + iv;
+            }
+        }
+        if (live) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const double t = fma((double)Lo[c], 0x1p-28, (double)H[c]);
+                const int ec = s_ec[c0 + c];
+                if (er == kBadExp || ec == kBadExp) {
+                    Crow[c0 + c] = __longlong_as_double(0x7ff8000000000000LL);
+                } else {
+                    const double scale = ldexp(1.0, max(-1074, min(1023, er + ec - 35)));
+                    Crow[c0 + c] = fma(-t, scale, Crow[c0 + c]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        if (s_abort) {
+            // a wait gave up: let copies and MMAs still in flight land first
+            const long long t0 = clock64();
+            while (clock64() - t0 < 4000000LL) {
+            }
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t oz_plane_bytes(int nt) { return (size_t)((int64_t)nt * T + T) * kRowBytes; }
+size_t oz_slice_bytes(int nt) { return kSlices * oz_plane_bytes(nt); }
+size_t oz_expo_ints(int nt) { return (size_t)((int64_t)nt * T + T); }
+
+cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E, int* err, cudaStream_t st,
+                             int64_t* launches) {
+    const int rem = nt - k - 1;
+    if (rem <= 0) return cudaSuccess;
+    static_assert(kOzSmem + 1024 <= 227 * 1024, "shared memory");
+    cudaError_t e = cudaFuncSetAttribute(oz_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    if (e != cudaSuccess) return e;
+    const size_t pb = oz_plane_bytes(nt);
+    const unsigned rows = (unsigned)((int64_t)rem * T);
+    oz_slice_kernel<<<dim3((rows + 7) / 8, (unsigned)g), 256, 0, st>>>(A, nt, k, pb, S, E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int64_t tiles = 0;
+    for (int u = 0; 2 * u < rem; ++u) tiles += std::min(2 * u + 2, rem);
+    oz_syrk_kernel<<<dim3((unsigned)tiles, (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace ap

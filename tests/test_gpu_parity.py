@@ -226,3 +226,30 @@ def test_sfu_rates_are_plausible():
     # every NVIDIA part, and neither exceeds the 128 lanes of an SM
     e, q = ap.ap_sfu_rates()
     assert 4.0 <= q <= 1.05 * e <= 1.05 * 128.0, (e, q)
+
+
+@pytest.mark.parametrize("n,d,b,kern,ell", [(1500, 5, 512, wl.MATERN52, (0.3, 3.0)),
+                                             (4096, 3, 2048, wl.RBF, (0.05, 0.2))])
+def test_tensor_core_cache_matches_fp64_cache(n, d, b, kern, ell):
+    # The trailing updates of the FP64 block Cholesky run either as FP64 FMAs or
+    # as exact integer slice products on the tensor cores; both caches hold the
+    # FP32-rounded inverse factor of nearly the same FP64 factor.  Each run of
+    # the same cyclic AP steps is within the FP32 form's replay bound of the
+    # exact iterate (2e-4 max|W|, test_ap_steps_match_oracle_replay), so the two
+    # agree to twice that.  (The bound presumes moderately conditioned blocks:
+    # FP32 inverse factors of a block with condition number kappa differ by up
+    # to kappa 2^-24 in the block solve, whichever FP64 factor they come from.)
+    # The second case factors blocks of 32 x 32 tiles with a ragged last block.
+    p = wl.random_problem(n, d, b, 4, kern, 0.01, 31, ell_range=ell)
+    m = -(-n // b)
+    Ws = []
+    for mode in (ap.AP_CACHE_TC_EXACT, ap.AP_CACHE_FP64):
+        opts = ap.ap_opts_default(block=b, select=ap.AP_SEL_CYCLIC, tol=1e-30, min_epochs=0, max_steps=3 * m,
+                                  cache_gemm=mode)
+        ctx = ap.ap_create(_t(p.X), ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean), opts)
+        st, W, info, _ = ap.ap_solve(ctx, _t(p.B))
+        assert info["steps"] == 3 * m
+        Ws.append(W.cpu().numpy().astype(np.float64))
+        ap.ap_destroy(ctx)
+    scale = np.abs(Ws[1]).max()
+    assert np.abs(Ws[0] - Ws[1]).max() <= 4e-4 * scale, np.abs(Ws[0] - Ws[1]).max() / scale
