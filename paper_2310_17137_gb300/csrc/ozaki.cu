@@ -47,7 +47,7 @@ constexpr int kSlabRows = 2 * T;                            // rows of a super-t
 constexpr uint32_t kPlaneA = kSlabRows * T * 2;             // 16 KB of BF16
 constexpr uint32_t kPlaneB = T * T * 2;                     // 8 KB
 constexpr uint32_t kOzSmem = kSlices * (kPlaneA + kPlaneB); // 192 KB
-constexpr int kOzThreads = 128;
+constexpr int kOzThreads = 256;  // 8 warps: two per tensor-memory lane quarter
 constexpr uint32_t kRowBytes = T * 2;                       // one slice row (64 BF16)
 constexpr int kBadExp = -(1 << 30);  // row exponent marking a non-finite panel row
 
@@ -165,15 +165,22 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
     const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, 0u, &s_abort, err));
     if (ok) tc_fence_after();
 
-    // epilogue: thread tid owns row r of the super-tile (tensor-memory lane tid)
-    const int64_t r = (int64_t)i0 * T + tid;
-    const int rtile = i0 + tid / T;
+    // epilogue: warp w owns tensor-memory lanes (rows) 32 (w % 4) .. + 31 and
+    // columns 32 (w / 4) .. + 31 of the super-tile
+    const int rl = 32 * (warp & 3) + (tid & 31);
+    const int64_t r = (int64_t)i0 * T + rl;
+    const int rtile = i0 + rl / T;
     const bool live = ok && rtile < nt && j <= rtile;
     const int er = live ? E[(int64_t)z * rows_pad + r] : 0;
     double* Crow = A + (int64_t)z * ld * ld + r * ld + (int64_t)j * T;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // exact conversions: an FP32 integer below 2^22 through the FP32 mantissa,
+    // a 64-bit integer below 2^51 through the FP64 mantissa
+    constexpr float kMagicF = 12582912.0f;                  // 1.5 * 2^23
+    constexpr long long kMagicDBits = 0x4338000000000000LL;  // 1.5 * 2^52
+    constexpr double kMagicD = 6755399441055744.0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < T; c0 += 16) {
+    for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32; c0 += 16) {
         long long H[16], Lo[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) H[c] = Lo[c] = 0;
@@ -189,7 +196,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
             }
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const long long iv = (long long)__float2int_rn(__uint_as_float(v[c]));
+                const long long iv =
+                    (long long)(__float_as_int(__uint_as_float(v[c]) + kMagicF) - __float_as_int(kMagicF));
                 if (L <= 5) H[c] = H[c] * 128 + iv;
                 else Lo[c] = Lo[c] * 128 + iv;
             }
@@ -197,14 +205,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
         if (live) {
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const double t = fma((double)Lo[c], 0x1p-28, (double)H[c]);
+                const double hd = __longlong_as_double(kMagicDBits + H[c]) - kMagicD;
+                const double ld_ = __longlong_as_double(kMagicDBits + Lo[c]) - kMagicD;
+                const double t = fma(ld_, 0x1p-28, hd);
                 const int ec = s_ec[c0 + c];
-                if (er == kBadExp || ec == kBadExp) {
-                    Crow[c0 + c] = __longlong_as_double(0x7ff8000000000000LL);
-                } else {
-                    const double scale = ldexp(1.0, max(-1074, min(1023, er + ec - 35)));
-                    Crow[c0 + c] = fma(-t, scale, Crow[c0 + c]);
-                }
+                const int e = er + ec - 35;
+                double scale;
+                if (e >= -1022 && e <= 1023) scale = __longlong_as_double((long long)(e + 1023) << 52);
+                else scale = ldexp(1.0, max(-1074, min(1023, e)));
+                const double nv = fma(-t, scale, Crow[c0 + c]);
+                Crow[c0 + c] = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000LL) : nv;
             }
         }
     }
