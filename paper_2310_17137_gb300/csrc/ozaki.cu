@@ -57,38 +57,73 @@ __device__ __forceinline__ size_t slice_off(int64_t row, int kk) {
     return ((size_t)((row >> 3) * 8 + (kk >> 3)) * 8 + (size_t)(row & 7)) * 16 + (size_t)(kk & 7) * 2;
 }
 
-// Slices of the panel (tile column k) for the trailing rows r >= 64 (k + 1):
-// one warp per row.
+// Slices of the panel (tile column k) for the trailing rows r >= 64 (k + 1),
+// in integer arithmetic on the FP64 bit patterns: eight threads per row, each
+// owning 8 consecutive K values (one 16-byte core row per slice plane).
+//   e_r  = (largest biased exponent of the row) - 1021, so |v| 2^-e_r < 1/2;
+//   X    = round(v 2^{56 - e_r}), an integer below 2^55 (values below 2^-1022
+//          are taken as 0);
+//   s_p  = round(t_p / 2^{56-7p}), t_{p+1} = t_p - s_p 2^{56-7p}, t_1 = X,
+// so that X = sum_p s_p 2^{56-7p} exactly with every |s_p| <= 64.
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* A, int nt, int k, size_t plane_bytes,
                                                        uint8_t* S, int* E) {
     const int z = blockIdx.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, grp = tid & 7;  // K values 8 grp .. 8 grp + 7
     const int64_t ld = (int64_t)nt * T;
-    const int64_t r = (int64_t)(k + 1) * T + (int64_t)blockIdx.x * 8 + warp;
-    if (r >= ld) return;
-    const double* row = A + (int64_t)z * ld * ld + r * ld + (int64_t)k * T;
-    double v[2] = {row[lane], row[lane + 32]};
-    double m = fmax(fabs(v[0]), fabs(v[1]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const bool nonfinite = __any_sync(0xffffffffu, !isfinite(v[0]) || !isfinite(v[1]));
-    int e = 0;
-    if (m > 0.0 && m <= 1.0e300) e = max(-1000, min(1000, ilogb(m) + 2));  // |v| 2^-e < 1/2
-    uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes;
+    const int64_t r = (int64_t)(k + 1) * T + (int64_t)blockIdx.x * 32 + (tid >> 3);
+    const bool live = r < ld;
+    long long bits[8];
+    if (live) {
+        const double2* src = reinterpret_cast<const double2*>(A + (int64_t)z * ld * ld + r * ld + (int64_t)k * T +
+                                                              8 * grp);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int kk = lane + 32 * h;
-        double x = scalbn(v[h], -e);
+        for (int h = 0; h < 4; ++h) {
+            const double2 v = src[h];
+            bits[2 * h] = __double_as_longlong(v.x);
+            bits[2 * h + 1] = __double_as_longlong(v.y);
+        }
+    } else {
 #pragma unroll
-        for (int p = 0; p < kSlices; ++p) {
-            const double t = x * 128.0;
-            const double s = rint(t);  // |s| <= 64
-            x = t - s;                 // exact
-            *reinterpret_cast<__nv_bfloat16*>(Sz + (size_t)p * plane_bytes + slice_off(r, kk)) =
-                __double2bfloat16(s);
+        for (int q = 0; q < 8; ++q) bits[q] = 0;
+    }
+    int ebmax = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ebmax = max(ebmax, (int)((bits[q] >> 52) & 0x7ff));
+    // the eight threads of a row are eight consecutive lanes
+    for (int o = 1; o < 8; o <<= 1) ebmax = max(ebmax, __shfl_xor_sync(0xffffffffu, ebmax, o));
+    if (!live) return;
+    const bool nonfinite = ebmax == 0x7ff;
+    const int e = ebmax - 1021;
+    uint32_t w[kSlices][4];  // BF16 pairs of the 8 values, per plane
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int eb = (int)((bits[q] >> 52) & 0x7ff);
+        long long X = 0;
+        if (eb != 0 && !nonfinite) {
+            const long long M = (bits[q] & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+            const int sh = eb - ebmax + 2;  // <= 2
+            if (sh >= 0) X = M << sh;
+            else if (-sh <= 60) X = (M + (1LL << (-sh - 1))) >> (-sh);
+            if (bits[q] < 0) X = -X;
+        }
+#pragma unroll
+        for (int p = 1; p <= kSlices; ++p) {
+            const int sft = 56 - 7 * p;
+            const long long sp = sft > 0 ? (X + (1LL << (sft - 1))) >> sft : X;
+            X -= sp << sft;
+            const float f = (float)(int)sp;
+            uint32_t hb;
+            asm("{\n\t.reg .b16 h;\n\tcvt.rn.bf16.f32 h, %1;\n\tmov.b32 %0, {h, h};\n\t}" : "=r"(hb) : "f"(f));
+            if (q & 1) w[p - 1][q >> 1] |= hb & 0xFFFF0000u;
+            else w[p - 1][q >> 1] = hb & 0x0000FFFFu;
         }
     }
+    uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes + slice_off(r, 8 * grp);
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p)
+        *reinterpret_cast<uint4*>(Sz + (size_t)p * plane_bytes) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
     // a NaN or infinity in the panel must reach the next pivot test as NaN
-    if (lane == 0) E[(int64_t)z * (ld + T) + r] = nonfinite ? kBadExp : e;
+    if (grp == 0) E[(int64_t)z * (ld + T) + r] = nonfinite ? kBadExp : e;
 }
 
 __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int nt, int k, const uint8_t* S,
@@ -248,7 +283,7 @@ cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E
     if (e != cudaSuccess) return e;
     const size_t pb = oz_plane_bytes(nt);
     const unsigned rows = (unsigned)((int64_t)rem * T);
-    oz_slice_kernel<<<dim3((rows + 7) / 8, (unsigned)g), 256, 0, st>>>(A, nt, k, pb, S, E);
+    oz_slice_kernel<<<dim3((rows + 31) / 32, (unsigned)g), 256, 0, st>>>(A, nt, k, pb, S, E);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int64_t tiles = 0;
     for (int u = 0; 2 * u < rem; ++u) tiles += std::min(2 * u + 2, rem);
