@@ -551,6 +551,54 @@ def run_serving(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_study(args) -> None:
+    """Selection rules and block sizes on the same kernels (the shape of the
+    paper's Sec. 3 block-selection comparison and of its block-size study), on
+    the Matern-5/2 generator at n = 65,536 in the tensor-core form: the true
+    relative residual after 1..32 epochs for Gauss-Southwell, cyclic and random
+    selection (b = 2048), and time and residual after 16 epochs for b = 1024 ..
+    8192 (cache included)."""
+    import torch
+    import paper_2310_17137_gb300 as ap
+    dev = torch.device("cuda", 0)
+    p = wl.matern52_ard(n=args.study_n)
+    X = torch.from_numpy(p.X).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+    rules = {"gauss_southwell": ap.AP_SEL_GS, "cyclic": ap.AP_SEL_CYCLIC, "random": ap.AP_SEL_RANDOM}
+    epochs = [1, 2, 4, 8, 16, 32]
+    sel = {}
+    for name, rule in rules.items():
+        rows = []
+        for e in epochs:
+            ctx = ap.ap_create(X, hyper, ap.ap_opts_default(block=2048, select=rule, tol=1e-30, min_epochs=e,
+                                                            max_epochs=e, precision=ap.AP_BF16_REFINE,
+                                                            refine_every=10, seed=5))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, info, _ = ap.ap_solve(ctx, B)
+            torch.cuda.synchronize()
+            rows.append({"epochs": e, "rel_res_y": info["rel_res_true"][0],
+                         "rel_res_max": max(info["rel_res_true"][:p.c]), "solve_s": time.perf_counter() - t0})
+            ap.ap_destroy(ctx)
+        sel[name] = rows
+    bs = []
+    for b in [1024, 2048, 4096, 8192]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = ap.ap_create(X, hyper, ap.ap_opts_default(block=b, tol=1e-30, min_epochs=16, max_epochs=16,
+                                                        precision=ap.AP_BF16_REFINE, refine_every=10))
+        _, _, info, _ = ap.ap_solve(ctx, B)
+        torch.cuda.synchronize()
+        bs.append({"block": b, "time_s": time.perf_counter() - t0, "cache_s": info["t_cache_s"],
+                   "solve_s": info["t_solve_s"], "rel_res_y": info["rel_res_true"][0],
+                   "rel_res_max": max(info["rel_res_true"][:p.c])})
+        ap.ap_destroy(ctx)
+    print(json.dumps({"metric": METRIC, "mode": "study", "workload": f"{p.name} ({wl.KERNEL_NAMES[p.kernel]} ARD, "
+                      f"c={p.c}, noise={p.noise:g}), BF16+refine form", "selection": sel, "block_size": bs}),
+          flush=True)
+
+
 def main():
     ap_ = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap_.add_argument("--gpus", type=int, default=1)
@@ -574,6 +622,8 @@ def main():
     ap_.add_argument("--no-ttt", action="store_true")
     ap_.add_argument("--no-mll", action="store_true", help="skip the MLL-gradient timing")
     ap_.add_argument("--serve", action="store_true", help="replay the serving workload instead")
+    ap_.add_argument("--study", action="store_true", help="selection rules and block sizes instead")
+    ap_.add_argument("--study-n", type=int, default=65536)
     ap_.add_argument("--serve-requests", type=int, default=512)
     ap_.add_argument("--serve-rate", type=float, default=40.0)
     ap_.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -585,6 +635,9 @@ def main():
     if args.serve:
         if rank == 0:
             run_serving(args)
+    elif args.study:
+        if rank == 0:
+            run_study(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
