@@ -42,6 +42,10 @@ struct ap_ctx {
     float *R = nullptr, *W = nullptr, *Bp = nullptr, *Z = nullptr, *Delta = nullptr, *Tmp = nullptr;
     double *part_norm = nullptr, *part_col = nullptr;
     int64_t part_alloc = 0;
+    // block-solve work split and partial sums
+    float* spart = nullptr;
+    unsigned* sticket = nullptr;
+    int sol_tpc = 1, sol_maxj = 1;
     // always-present device scalars
     double *norms = nullptr, *colnorm = nullptr, *gout = nullptr, *gpart = nullptr;
     int64_t gpart_alloc = 0;
@@ -337,6 +341,8 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         dfree(ctx, ctx->Delta);
         dfree(ctx, ctx->Tmp);
         dfree(ctx, ctx->part_col);
+        dfree(ctx, ctx->spart);
+        dfree(ctx, ctx->sticket);
         ctx->Cp = 0;
         const size_t nc = (size_t)(ctx->n * Cp);
         AP_TRY(dalloc_t(ctx, &ctx->R, nc));
@@ -345,6 +351,10 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         AP_TRY(dalloc_t(ctx, &ctx->Tmp, nc));
         AP_TRY(dalloc_t(ctx, &ctx->Z, (size_t)ctx->nt * kTile * Cp));
         AP_TRY(dalloc_t(ctx, &ctx->Delta, (size_t)ctx->b * Cp));
+        block_solve_layout(ctx->nt, ctx->num_sms, &ctx->sol_tpc, &ctx->sol_maxj);
+        AP_TRY(dalloc_t(ctx, &ctx->spart, (size_t)ctx->nt * ctx->sol_maxj * kTile * std::max(Cp, 4)));
+        AP_TRY(dalloc_t(ctx, &ctx->sticket, (size_t)ctx->nt));
+        AP_CK(cudaMemsetAsync(ctx->sticket, 0, sizeof(unsigned) * ctx->nt, ctx->st));
         const Shape a = step_shape(ctx, Cp, ctx->b), b = step_shape(ctx, Cp, ctx->n), c = norm_shape(ctx);
         const Shape d = comp_shape(ctx, ctx->n);
         int64_t need = std::max(std::max(a.ntiles * a.S, b.ntiles * b.S), std::max(c.ntiles, d.ntiles * d.S));
@@ -382,6 +392,10 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
     sp.step_ctr = ctx->step;
     sp.trace = ctx->trace;
     sp.trace_cap = ctx->trace_alloc;
+    sp.tpc = ctx->sol_tpc;
+    sp.maxj = ctx->sol_maxj;
+    sp.spart = ctx->spart;
+    sp.sticket = ctx->sticket;
     AP_CK(launch_block_solve(sp, ctx->st, &ctx->launches));
     if (ctx->tc) {
         AP_CK(launch_tc_pack_delta(ctx->Delta, ctx->b, Cp, ctx->cpb, ctx->DT, ctx->st));

@@ -131,7 +131,13 @@ struct SolveParams {
     const int64_t* step_ctr;
     int* trace;            // device trace or nullptr
     int64_t trace_cap;
+    int tpc;               // tiles per CTA (block_solve_layout)
+    int maxj;              // partial slots per output row of tiles
+    float* spart;          // nt * maxj * 64 * max(C, 4) floats of partial sums
+    unsigned* sticket;     // nt tickets, zero between launches
 };
+// Work split of the block solve for nt tiles per block edge on num_sms SMs.
+void block_solve_layout(int nt, int num_sms, int* tpc, int* maxj);
 cudaError_t launch_block_solve(const SolveParams& p, cudaStream_t st, int64_t* launches);
 
 // ---- small helpers ----------------------------------------------------------
