@@ -20,11 +20,15 @@ import workloads as wl
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    # n, d, b, c, kernel: several 128-row tiles and 64-column chunks, ragged tails
+    # n, d, b, c, kernel: several 128-row tiles and 128-column chunks, ragged
+    # tails; distance operands of K = 16, 32, 64, 48 and 96 (3d + 4 rounded up to
+    # 16; d = 30 is the largest the tensor-core form takes, with the largest
+    # shared-memory stages at c = 32)
     (1000, 3, 256, 16, wl.MATERN52),
     (1337, 5, 300, 3, wl.RBF),
     (777, 17, 192, 32, wl.MATERN32),
     (2100, 11, 512, 16, wl.RBF),
+    (900, 30, 384, 32, wl.MATERN52),
 ]
 
 
