@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             const int64_t i = r0 + quarter * 32 + lane;
             const bool live = ok && i < seg_hi;
             const bool diag = i >= col0 && i < col0 + ncols;
-            double sq = 0.0;
+            // squares are summed in FP32 within a thread and a warp (at most 32 terms
+            // each, relative error below 2e-6) and in FP64 beyond: FP64 arithmetic is
+            // scarce on this part
+            float sqf = 0.0f;
             // 16 columns at a time: sum the three accumulators, update R, norms
 #pragma unroll 1
             for (int c0 = 0; c0 < C; c0 += 16) {
@@ -376,18 +379,19 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                         v = fmaf(-p.s, a16[k], p.R[i * C + c]);
                         if (diag) v = fmaf(-p.noise, p.Delta[(i - col0) * C + c], v);
                         p.R[i * C + c] = v;
-                        sq += (double)v * (double)v;
+                        sqf = fmaf(v, v, sqf);
                     }
                     if (e.flags & kEpiColNorms) {
-                        double w = (double)v * (double)v;
+                        float w = v * v;
                         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
-                        if (lane == 0) s_colred[warp][c0 + k] = w;
+                        if (lane == 0) s_colred[warp][c0 + k] = (double)w;
                     }
                 }
             }
             if (ok) tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_acc_free);
+            double sq = sqf;
             for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
             if (lane == 0) red_d[warp] = sq;
             asm volatile("bar.sync 1, 128;" ::: "memory");
