@@ -323,14 +323,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         }
     } else {
         // ------------------------------------------------ transform warps
-        // Work unit = half a warp's columns of a chunk (16 entries per thread).
-        // Software pipelined: while unit u is transformed, the tensor-memory load
-        // of unit u + 1 is already in flight.
+        // Per chunk a warp takes its 32 columns as two 16-column units (16 entries
+        // per thread each): both tensor-memory loads are in flight together and the
+        // two units are transformed interleaved (the other warps of the scheduler
+        // cover the load latency).
         const int quarter = warp & 3, group = warp >> 2;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const int total = (int)(my_tiles * nq);  // chunks of this CTA (< 2^31)
         bool ok = total > 0;
-        uint32_t ta[16], tb[16];
         // columns of unit (chunk c, unit h of this warp): S there is replaced by [P_hi | P_lo]
         auto u_addr = [&](int c, int h) -> uint32_t {
             return tmem + lane_base + (uint32_t)(kChunk * (c % kBufs) + kColsPerWarp * group + 16 * h);
@@ -405,61 +405,47 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         };
         int q_in_tile = 0;  // chunk index within the current tile
         int64_t tile_no = 0;
-        // one unit: S of (c, h) is in `cur` (load issued); prefetch the next unit
-        // into `nxt`, transform, store P in place; after the last unit of a chunk
-        // signal the contraction MMA
-        auto unit = [&](int c, int h, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
-            tmem_wait_ld();
-            if (h + 1 < kUnits) {
-                if (ok) tmem_ld16(u_addr(c, h + 1), nxt);
-            } else if (c + 1 < total) {
-                if (ok)
-                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[(c + 1) % kBufs],
-                                                          (uint32_t)(((c + 1) / kBufs) & 1), &s_abort, p.err));
-                if (ok) {
-                    tc_fence_after();
-                    tmem_ld16(u_addr(c + 1, 0), nxt);
-                }
-            }
-            uint32_t pw[16];  // [P_hi words | P_lo words]
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float2 v = phi_tc2<KERN>(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
-                const uint32_t hw = pack_bf16(v.x, v.y);
-                pw[k] = hw;
-                const float2 lo = sub2(v, make_float2(bf16_lo_to_f32(hw), bf16_hi_to_f32(hw)));
-                pw[8 + k] = pack_bf16(lo.x, lo.y);
-            }
-            if (ok) tmem_st16(u_addr(c, h), pw);
-            if (h == kUnits - 1) {
-                if (ok) {
-                    tmem_wait_st();
-                    tc_fence_before();
-                }
-                __syncwarp();
-                if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs][group]);
-                if (++q_in_tile == nq) {
-                    if (warp < 4) epilogue(tile_no);
-                    q_in_tile = 0;
-                    ++tile_no;
-                }
-            }
-        };
-        if (ok) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[0], 0u, &s_abort, p.err));
+        static_assert(kUnits == 2, "two units per warp and chunk");
+        // one chunk: both 16-column units loaded together, transformed together,
+        // stored in place; then signal the contraction MMA
+        for (int c = 0; c < total; ++c) {
+            uint32_t ta[16], tb[16];
+            if (ok)
+                ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[c % kBufs], (uint32_t)((c / kBufs) & 1),
+                                                      &s_abort, p.err));
             if (ok) {
                 tc_fence_after();
-                tmem_ld16(u_addr(0, 0), ta);
+                tmem_ld16(u_addr(c, 0), ta);
+                tmem_ld16(u_addr(c, 1), tb);
+                tmem_wait_ld();
+            }
+            uint32_t pa[16], pb[16];  // [P_hi words | P_lo words] of each unit
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float2 v = phi_tc2<KERN>(__uint_as_float(ta[2 * k]), __uint_as_float(ta[2 * k + 1]));
+                const float2 w = phi_tc2<KERN>(__uint_as_float(tb[2 * k]), __uint_as_float(tb[2 * k + 1]));
+                const uint32_t hv = pack_bf16(v.x, v.y), hw = pack_bf16(w.x, w.y);
+                pa[k] = hv;
+                pb[k] = hw;
+                const float2 lv = sub2(v, make_float2(bf16_lo_to_f32(hv), bf16_hi_to_f32(hv)));
+                const float2 lw = sub2(w, make_float2(bf16_lo_to_f32(hw), bf16_hi_to_f32(hw)));
+                pa[8 + k] = pack_bf16(lv.x, lv.y);
+                pb[8 + k] = pack_bf16(lw.x, lw.y);
+            }
+            if (ok) {
+                tmem_st16(u_addr(c, 0), pa);
+                tmem_st16(u_addr(c, 1), pb);
+                tmem_wait_st();
+                tc_fence_before();
+            }
+            __syncwarp();
+            if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs][group]);
+            if (++q_in_tile == nq) {
+                if (warp < 4) epilogue(tile_no);
+                q_in_tile = 0;
+                ++tile_no;
             }
         }
-        // every chunk is visited even after a failed wait (without touching tensor
-        // memory), so warps 0-3 make the same number of epilogue calls
-        const int total_units = total * kUnits;
-        for (int u = 0; u < total_units; u += 2) {
-            unit(u / kUnits, u % kUnits, ta, tb);
-            if (u + 1 < total_units) unit((u + 1) / kUnits, (u + 1) % kUnits, tb, ta);
-        }
-        tmem_wait_ld();
     }
     // ---------------------------------------------------------- teardown
     __syncwarp();
