@@ -255,6 +255,18 @@ int64_t ap_launch_count(const ap_ctx* ctx);
  * AP_ERR_CUDA on device errors. */
 ap_status ap_sfu_rates(double* ex2_per_clk_sm, double* sqrt_per_clk_sm);
 
+/* The kernel profile phi(r^2) in FP64 exactly as the Cholesky cache evaluates
+ * it on the device when it builds the diagonal blocks K_II (Sec. 3, "Cached
+ * Cholesky Factors"; phi of Sec. 5: RBF e^{-r^2/2}, Matern-3/2 (1 + u) e^{-u}
+ * with u = sqrt(3) r, Matern-5/2 (1 + u + u^2/3) e^{-u} with u = sqrt(5) r),
+ * for verification against a host math library.  r2_host and phi_host are
+ * host arrays of count doubles (r2 >= 0, finite); the call copies them through
+ * device memory it allocates and frees, on the current device, and returns
+ * when phi_host is written.  AP_ERR_INVALID_ARG for an unknown kernel, a
+ * negative count or NULL arrays with count > 0; AP_ERR_NOMEM / AP_ERR_CUDA on
+ * device errors. */
+ap_status ap_phi_fp64_eval(int32_t kernel, const double* r2_host, int64_t count, double* phi_host);
+
 /* ------------------------------------------------------------------ serving
  * Continuous batching of GP solve + posterior-mean requests (no counterpart in
  * the paper, which solves one system at a time): requests are admitted in

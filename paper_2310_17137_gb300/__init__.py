@@ -28,7 +28,7 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_IN
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
+           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
 
 
 class ApError(RuntimeError):
@@ -227,6 +227,17 @@ def ap_sfu_rates() -> tuple:
     if st != AP_OK:
         raise ApError(st, "ap_sfu_rates")
     return e.value, q.value
+
+
+def ap_phi_fp64_eval(kernel: int, r2) -> np.ndarray:
+    """FP64 phi(r^2) as the Cholesky cache evaluates it on the device."""
+    r2 = np.ascontiguousarray(r2, dtype=np.float64).ravel()
+    out = np.empty_like(r2)
+    st = _capi.load().ap_phi_fp64_eval(int(kernel), r2.ctypes.data_as(ctypes.c_void_p), r2.size,
+                                       out.ctypes.data_as(ctypes.c_void_p))
+    if st != AP_OK:
+        raise ApError(st, "ap_phi_fp64_eval")
+    return out
 
 
 def ap_destroy(ctx: Context) -> None:

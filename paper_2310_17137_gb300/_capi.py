@@ -24,7 +24,7 @@ AP_RESID_AUTO, AP_RESID_FP32, AP_RESID_COMPENSATED = 0, 1, 2
 # every function include/ap.h declares
 EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_residual",
            "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy", "ap_status_str",
-           "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count", "ap_sfu_rates",
+           "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval",
            "ap_grad_quadforms_static", "ap_server_create", "ap_server_submit", "ap_server_poll",
            "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result"]
 
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_destroy": (None, [P]),
         "ap_launch_count": (i64, [P]),
         "ap_sfu_rates": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "ap_phi_fp64_eval": (st, [i32, P, i64, P]),
         "ap_server_create": (st, [ctypes.POINTER(P), ctypes.c_size_t, i32, i32]),
         "ap_server_submit": (st, [P, ctypes.POINTER(ap_request), ctypes.POINTER(i64)]),
         "ap_server_poll": (st, [P, i64, ctypes.POINTER(ap_request_result)]),

@@ -1065,6 +1065,30 @@ ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const f
 
 int64_t ap_launch_count(const ap_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+ap_status ap_phi_fp64_eval(int32_t kernel, const double* r2_host, int64_t count, double* phi_host) {
+    if (kernel < AP_RBF || kernel > AP_MATERN52 || count < 0) return AP_ERR_INVALID_ARG;
+    if (count == 0) return AP_OK;
+    if (!r2_host || !phi_host) return AP_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)count;
+    double* d_r2 = nullptr;
+    double* d_out = nullptr;
+    if (cudaMalloc(&d_r2, bytes) != cudaSuccess || cudaMalloc(&d_out, bytes) != cudaSuccess) {
+        cudaFree(d_r2);
+        cudaGetLastError();
+        return AP_ERR_NOMEM;
+    }
+    cudaError_t err = cudaMemcpy(d_r2, r2_host, bytes, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = launch_phi_fp64_eval(kernel, d_r2, count, d_out, 0);
+    if (err == cudaSuccess) err = cudaMemcpy(phi_host, d_out, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d_r2);
+    cudaFree(d_out);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return AP_ERR_CUDA;
+    }
+    return AP_OK;
+}
+
 void ap_destroy(ap_ctx* ctx) {
     if (!ctx) return;
     if (ctx->st) cudaStreamSynchronize(ctx->st);

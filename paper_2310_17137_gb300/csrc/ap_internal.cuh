@@ -102,18 +102,23 @@ struct CacheParams {
 // Factor blocks [blk0, blk0 + g) into the packed FP32 inverse factors Linv.
 // A (g * (nt*64)^2 doubles) and Dinv (g * nt * 64^2 doubles) are work buffers.
 // bad (g ints) gets 1 for a block whose factorisation met a non-positive pivot.
-// Tensor-core trailing updates with FP64 results (ozaki.cu): slice planes of
+// Tensor-core panel solves and trailing updates with FP64 results (ozaki.cu): slice planes of
 // oz_slice_bytes(nt) bytes and oz_expo_ints(nt) row exponents per block.
 size_t oz_slice_bytes(int nt);
 size_t oz_expo_ints(int nt);
 cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E, int* err, cudaStream_t st,
                              int64_t* launches);
-// Work buffers of the tensor-core trailing updates; null = FP64 FMA updates.
+// The panel solve A_ik := A_ik L_kk^{-T} (i > k) the same way, L_kk^{-1} from Dinv.
+cudaError_t launch_oz_trsm(double* A, const double* Dinv, int nt, int k, int g, uint8_t* S, int* E, int* err,
+                           cudaStream_t st, int64_t* launches);
+// Work buffers of the tensor-core panel solves and trailing updates; null = FP64 FMA.
 struct OzWork {
     uint8_t* S;  // g * oz_slice_bytes(nt)
     int* E;      // g * oz_expo_ints(nt)
     int* err;    // wait-timeout flag
 };
+// FP64 phi of the cache build at count squared distances (device arrays).
+cudaError_t launch_phi_fp64_eval(int kernel, const double* r2, int64_t count, double* out, cudaStream_t st);
 cudaError_t cache_factor_group(const CacheParams& cp, int64_t blk0, int g, double* A, double* Dinv,
                                float* Linv, int* bad, const OzWork* oz, cudaStream_t st, int64_t* launches);
 

@@ -1,6 +1,7 @@
 // Trailing update of the tiled FP64 Cholesky (Sec. 3, "Cached Cholesky
-// Factors"; the SYRK/GEMM step carries b^3/3 of the factorisation's flops) on
-// the tensor cores, with FP64 results.
+// Factors"; the SYRK/GEMM step carries b^3/3 of the factorisation's flops) and
+// its panel solve (TRSM as the product A_ik L_kk^{-T}) on the tensor cores,
+// with FP64 results.
 //
 // A_ij -= A_ik A_jk^T for the trailing tiles k < j <= i is an FP64 dot product
 // of length 64 per entry.  GB300 runs FP64 at about 2 FMA per clock per SM, so
@@ -65,17 +66,17 @@ __device__ __forceinline__ size_t slice_off(int64_t row, int kk) {
 //          are taken as 0);
 //   s_p  = round(t_p / 2^{56-7p}), t_{p+1} = t_p - s_p 2^{56-7p}, t_1 = X,
 // so that X = sum_p s_p 2^{56-7p} exactly with every |s_p| <= 64.
-__global__ void __launch_bounds__(256) oz_slice_kernel(const double* A, int nt, int k, size_t plane_bytes,
-                                                       uint8_t* S, int* E) {
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* src0, int64_t zstride, int64_t sld,
+                                                       int64_t nrows, int64_t row0, int64_t rows_pad,
+                                                       size_t plane_bytes, uint8_t* S, int* E) {
     const int z = blockIdx.y;
     const int tid = threadIdx.x, grp = tid & 7;  // K values 8 grp .. 8 grp + 7
-    const int64_t ld = (int64_t)nt * T;
-    const int64_t r = (int64_t)(k + 1) * T + (int64_t)blockIdx.x * 32 + (tid >> 3);
-    const bool live = r < ld;
+    const int64_t rr = (int64_t)blockIdx.x * 32 + (tid >> 3);
+    const int64_t r = row0 + rr;  // row of the slice planes
+    const bool live = rr < nrows;
     long long bits[8];
     if (live) {
-        const double2* src = reinterpret_cast<const double2*>(A + (int64_t)z * ld * ld + r * ld + (int64_t)k * T +
-                                                              8 * grp);
+        const double2* src = reinterpret_cast<const double2*>(src0 + (int64_t)z * zstride + rr * sld + 8 * grp);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const double2 v = src[h];
@@ -123,10 +124,15 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* A, int nt, 
     for (int p = 0; p < kSlices; ++p)
         *reinterpret_cast<uint4*>(Sz + (size_t)p * plane_bytes) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
     // a NaN or infinity in the panel must reach the next pivot test as NaN
-    if (grp == 0) E[(int64_t)z * (ld + T) + r] = nonfinite ? kBadExp : e;
+    if (grp == 0) E[(int64_t)z * rows_pad + r] = nonfinite ? kBadExp : e;
 }
 
-__global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int nt, int k, const uint8_t* S,
+// kTrsm = false: A_ij -= A_ik A_jk^T over the trailing lower tiles (SYRK/GEMM);
+// kTrsm = true:  A_ik := A_ik L_kk^{-T} for the panel tiles i > k (TRSM as a
+// product with the inverse diagonal tile, whose slices sit in the plane rows
+// of tile k), written instead of subtracted.
+template <bool kTrsm>
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(double* A, int nt, int k, const uint8_t* S,
                                                                size_t plane_bytes, const int* E, int* err) {
     extern __shared__ __align__(1024) uint8_t oz_smem[];
     __shared__ __align__(8) uint64_t bar_load, bar_mma;
@@ -136,13 +142,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
     const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
     const int rem = nt - k - 1;
     // super-tile (u, jj) of this CTA: row tiles i0 = k + 1 + 2u, i0 + 1 and
-    // column tile j = k + 1 + jj <= i0 + 1
+    // column tile j = k + 1 + jj <= i0 + 1 (SYRK) or j = k (TRSM)
     int u = 0, jj = (int)blockIdx.x;
-    while (true) {
-        const int nc = min(2 * u + 2, rem);
-        if (jj < nc) break;
-        jj -= nc;
-        ++u;
+    if constexpr (kTrsm) {
+        u = jj;
+        jj = -1;
+    } else {
+        while (true) {
+            const int nc = min(2 * u + 2, rem);
+            if (jj < nc) break;
+            jj -= nc;
+            ++u;
+        }
     }
     const int i0 = k + 1 + 2 * u, j = k + 1 + jj;
     const int64_t ld = (int64_t)nt * T, rows_pad = ld + T;
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
     const int rl = 32 * (warp & 3) + (tid & 31);
     const int64_t r = (int64_t)i0 * T + rl;
     const int rtile = i0 + rl / T;
-    const bool live = ok && rtile < nt && j <= rtile;
+    const bool live = ok && rtile < nt && (kTrsm || j <= rtile);
     const int er = live ? E[(int64_t)z * rows_pad + r] : 0;
     double* Crow = A + (int64_t)z * ld * ld + r * ld + (int64_t)j * T;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_syrk_kernel(double* A, int n
                 double scale;
                 if (e >= -1022 && e <= 1023) scale = __longlong_as_double((long long)(e + 1023) << 52);
                 else scale = ldexp(1.0, max(-1074, min(1023, e)));
-                const double nv = fma(-t, scale, Crow[c0 + c]);
+                const double nv = kTrsm ? t * scale : fma(-t, scale, Crow[c0 + c]);
                 Crow[c0 + c] = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000LL) : nv;
             }
         }
@@ -279,16 +290,42 @@ cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E
     const int rem = nt - k - 1;
     if (rem <= 0) return cudaSuccess;
     static_assert(kOzSmem + 1024 <= 227 * 1024, "shared memory");
-    cudaError_t e = cudaFuncSetAttribute(oz_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
     if (e != cudaSuccess) return e;
     const size_t pb = oz_plane_bytes(nt);
-    const unsigned rows = (unsigned)((int64_t)rem * T);
-    oz_slice_kernel<<<dim3((rows + 31) / 32, (unsigned)g), 256, 0, st>>>(A, nt, k, pb, S, E);
+    const int64_t ld = (int64_t)nt * T;
+    const int64_t rows = (int64_t)rem * T;
+    oz_slice_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)g), 256, 0, st>>>(
+        A + (int64_t)(k + 1) * T * ld + (int64_t)k * T, ld * ld, ld, rows, (int64_t)(k + 1) * T, ld + T, pb, S, E);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int64_t tiles = 0;
     for (int u = 0; 2 * u < rem; ++u) tiles += std::min(2 * u + 2, rem);
-    oz_syrk_kernel<<<dim3((unsigned)tiles, (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err);
+    oz_gemm_kernel<false><<<dim3((unsigned)tiles, (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err);
     if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_trsm(double* A, const double* Dinv, int nt, int k, int g, uint8_t* S, int* E, int* err,
+                           cudaStream_t st, int64_t* launches) {
+    const int rem = nt - k - 1;
+    if (rem <= 0) return cudaSuccess;
+    cudaError_t e =
+        cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    if (e != cudaSuccess) return e;
+    const size_t pb = oz_plane_bytes(nt);
+    const int64_t ld = (int64_t)nt * T;
+    const int64_t rows = (int64_t)rem * T;
+    // the panel below the diagonal tile, and L_kk^{-1} into the plane rows of tile k
+    oz_slice_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)g), 256, 0, st>>>(
+        A + (int64_t)(k + 1) * T * ld + (int64_t)k * T, ld * ld, ld, rows, (int64_t)(k + 1) * T, ld + T, pb, S, E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    oz_slice_kernel<<<dim3(T / 32, (unsigned)g), 256, 0, st>>>(Dinv + (int64_t)k * T * T, (int64_t)nt * T * T, T,
+                                                                T, (int64_t)k * T, ld + T, pb, S, E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    oz_gemm_kernel<true><<<dim3((unsigned)((rem + 1) / 2), (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb,
+                                                                                                    E, err);
+    if (launches) *launches += 3;
     return cudaGetLastError();
 }
 

@@ -221,6 +221,35 @@ def test_warm_start_resumes():
     assert np.max(np.linalg.norm(R, axis=0) / np.linalg.norm(p.B, axis=0)) <= 2e-5
 
 
+@pytest.mark.parametrize("kern", [wl.RBF, wl.MATERN32, wl.MATERN52])
+def test_cache_phi_fp64_matches_libm(kern):
+    # The cache builds K_II with its own FP64 exp (table-driven, Tang 1989) and
+    # Newton-refined sqrt.  Against the host libm on identical r^2: the exp and
+    # the polynomial contribute a few ulp, and the sqrt's last-bit error moves
+    # e^-u by a relative u * 2^-53 (the conditioning of e^-u), so
+    # |phi_gpu - phi| <= (6 + u) 2^-53 phi wherever phi is a normal double.
+    rng = np.random.default_rng(7)
+    r2 = np.concatenate([[0.0, 1e-300, 1e-40, 1e-30, 1e-12, 1e-6, 0.5, 1.0, 2.0, 1e3, 1e5, 1e13],
+                         10.0 ** rng.uniform(-8, 5, 20000), rng.uniform(0, 50, 20000)])
+    got = ap.ap_phi_fp64_eval(kern, r2)
+    if kern == wl.RBF:
+        u = np.zeros_like(r2)
+        ref = np.exp(-0.5 * r2)
+    elif kern == wl.MATERN32:
+        u = np.sqrt(3.0 * r2)
+        ref = (1.0 + u) * np.exp(-u)
+    else:
+        u = np.sqrt(5.0 * r2)
+        ref = (1.0 + u + u * u / 3.0) * np.exp(-u)
+    if kern == wl.RBF:
+        u = 0.5 * r2  # e^{-x}: the rounding of x = r^2/2 is shared, the reduction is exact to x 2^-53
+    normal = ref > 1e-300
+    bound = (6.0 + u) * 2.0 ** -53 * ref
+    assert np.all(np.abs(got - ref)[normal] <= bound[normal]), np.max((np.abs(got - ref) / bound)[normal])
+    assert np.all(got[~normal] <= 1e-290) and np.all(got >= 0)
+    assert got[0] == 1.0
+
+
 def test_sfu_rates_are_plausible():
     # per-SM-clock rates of the probe; exp2 runs at least as fast as sqrt on
     # every NVIDIA part, and neither exceeds the 128 lanes of an SM
