@@ -109,22 +109,25 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return d;
 }
 
-// phi of two distances at once: the SFU work per lane, the polynomial paired.
+// phi of two distances at once: the SFU work per lane, the Matern polynomial in
+// scalar FMAs (their constants are immediate operands; the paired form needs
+// them in register pairs and measured slower).
 template <int KERN>
 __device__ __forceinline__ float2 phi_tc2(float t0, float t1) {
     if constexpr (KERN == AP_RBF) {
         return make_float2(ex2_approx(-t0), ex2_approx(-t1));
     } else {
-        const float2 u = make_float2(sqrt_approx(fabsf(t0)), sqrt_approx(fabsf(t1)));
-        const float2 ex = make_float2(ex2_approx(-u.x), ex2_approx(-u.y));
-        const float2 one = make_float2(1.0f, 1.0f);
-        float2 poly;
+        const float u0 = sqrt_approx(fabsf(t0)), u1 = sqrt_approx(fabsf(t1));
+        const float e0 = ex2_approx(-u0), e1 = ex2_approx(-u1);
+        float p0, p1;
         if constexpr (KERN == AP_MATERN32) {
-            poly = fma2(u, make_float2(kInvL, kInvL), one);
+            p0 = fmaf(u0, kInvL, 1.0f);
+            p1 = fmaf(u1, kInvL, 1.0f);
         } else {
-            poly = fma2(u, fma2(u, make_float2(kInvL2Third, kInvL2Third), make_float2(kInvL, kInvL)), one);
+            p0 = fmaf(fmaf(u0, kInvL2Third, kInvL), u0, 1.0f);
+            p1 = fmaf(fmaf(u1, kInvL2Third, kInvL), u1, 1.0f);
         }
-        return mul2(poly, ex);
+        return make_float2(p0 * e0, p1 * e1);
     }
 }
 
