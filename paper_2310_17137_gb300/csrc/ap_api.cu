@@ -70,6 +70,8 @@ struct ap_ctx {
     int kd = 16, cpb = 0, num_sms = 152;
     int64_t tps128 = 0;
     uint8_t *XA = nullptr, *XB = nullptr, *DT = nullptr;
+    float* tc_scr = nullptr;  // boundary slots of tiles shared by two CTAs
+    int* tc_tick = nullptr;
     int* tc_err = nullptr;
     int64_t launches = 0;
     cudaError_t last_cuda = cudaSuccess;
@@ -424,6 +426,8 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
         tl.noise = ctx->noise;
         tl.sel = ctx->sel;
         tl.err = ctx->tc_err;
+        tl.scr = ctx->tc_scr;
+        tl.tick = ctx->tc_tick;
         tl.epi = make_epi(ctx, kEpiBlockNorms | (colnorms ? kEpiColNorms : 0), 1, sh);
         const int grid = (int)std::min<int64_t>(ctx->num_sms, sh.ntiles);
         AP_CK(launch_kmv_tc_step(ctx->kernel, tl, ctx->kd, Cp, grid, ctx->st));
@@ -604,6 +608,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
     AP_CK(cudaMemsetAsync(ctx->step, 0, sizeof(int64_t), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st));
+    if (ctx->tc_tick) AP_CK(cudaMemsetAsync(ctx->tc_tick, 0, sizeof(int) * ctx->num_sms, ctx->st));
     // ||b_c|| for the relative residuals
     AP_TRY(launch_norms(ctx, ctx->Bp, kEpiColNorms));
     double bn[AP_MAX_RHS] = {}, rn[AP_MAX_RHS] = {};
@@ -874,6 +879,13 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     if (ctx->tc) {
         if ((s = dalloc_t(ctx, &ctx->XA, tc_rows_bytes(ctx->m * ctx->tps128, ctx->kd))) != AP_OK) return fail(s);
         if ((s = dalloc_t(ctx, &ctx->XB, tc_cols_bytes(ctx->m, ctx->cpb, ctx->kd))) != AP_OK) return fail(s);
+        if ((s = dalloc_t(ctx, &ctx->tc_scr, tc_share_bytes(ctx->num_sms, AP_MAX_RHS) / sizeof(float))) != AP_OK)
+            return fail(s);
+        if ((s = dalloc_t(ctx, &ctx->tc_tick, (size_t)ctx->num_sms)) != AP_OK) return fail(s);
+        if (cudaMemsetAsync(ctx->tc_tick, 0, sizeof(int) * ctx->num_sms, ctx->st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(AP_ERR_CUDA);
+        }
     }
     if (cudaMemsetAsync(ctx->ticket, 0, 4 * sizeof(unsigned), ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st) != cudaSuccess ||

@@ -209,8 +209,12 @@ struct TcLaunch {
     float s, noise;
     const int* sel;
     int* err;
+    float* scr;  // grid x 2 x 128 x C floats (tc_share_bytes)
+    int* tick;   // grid ints, zero
     EpiParams epi;
 };
+// Boundary slots of the tensor-core update for a grid of CTAs and C right-hand sides.
+size_t tc_share_bytes(int grid, int C);
 cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int grid, cudaStream_t st);
 
 // Read-only view of what the gradient kernel needs from a context.

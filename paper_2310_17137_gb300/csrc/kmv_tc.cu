@@ -30,6 +30,13 @@
 // that read its P has completed), operands in a ring of shared-memory stages;
 // everything is synchronised by mbarriers, and every wait is bounded in time
 // and reports a timeout through the error flag instead of hanging.
+//
+// Work split: the (tile, chunk) pairs of a step, in tile-major order, are cut
+// into one equal contiguous range per persistent CTA (instead of whole tiles,
+// which leave the last wave partly idle: 2048 tiles on 152 SMs are 13.5 each).
+// A tile that straddles two ranges is accumulated in two parts; both go to a
+// boundary slot in global memory and the second CTA to arrive (an atomic
+// ticket, no waiting) adds them in a fixed order and updates R.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -146,6 +153,8 @@ struct TcParams {
     float s, noise;
     const int* sel;
     int* err;              // timeout flag
+    float* scr;            // gridDim.x x 2 x 128 x C: partial accumulators of the tiles two CTAs share
+    int* tick;             // gridDim.x arrival counters of those tiles (0 between launches)
     EpiParams epi;         // tiles of 128 rows aligned to blocks (tiles_per_seg = ceil(b / 128))
 };
 
@@ -176,6 +185,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     __shared__ int red_i[32];
     __shared__ double s_colred[4][C];
     __shared__ int s_last;
+    __shared__ int s_fin;  // this CTA completes a shared tile
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -186,7 +196,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     const int64_t ncols = min(p.b, p.n - col0);
     const int nq = (int)((ncols + kChunk - 1) / kChunk);
     const int64_t ntiles = e.ntiles;
-    const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // Work units are (tile, chunk) pairs in tile-major order, split into equal
+    // contiguous ranges, one per CTA.  With gridDim.x <= ntiles every range holds
+    // at least nq units, so a tile is shared by at most two CTAs (the end of one
+    // range and the start of the next); their partial accumulators meet in a
+    // boundary slot and the second to arrive updates R.  A "segment" is the part
+    // of one tile inside this CTA's range.
+    const int64_t U = ntiles * nq;
+    const int64_t u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+    const int64_t total = u1 - u0;
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -220,22 +238,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
 
     if (warp == kCopyWarp) {
         // ------------------------------------------------ bulk-copy issuer
-        if (lane == 0 && my_tiles > 0 && nq > 0) {
-            const int64_t total_chunks = my_tiles * nq;
-            auto issue_xa = [&](int64_t tt) -> bool {
-                const int xb = (int)(tt & 1);
-                const int64_t u = tt >> 1;
+        if (lane == 0 && total > 0) {
+            auto issue_xa = [&](int64_t sg, int64_t tile) -> bool {
+                const int xb = (int)(sg & 1);
+                const int64_t u = sg >> 1;
                 if (u >= 1 && !mbar_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1), &s_abort, p.err)) return false;
-                const int64_t tile = blockIdx.x + tt * gridDim.x;
                 mbar_expect_tx(&bar_xa_full[xb], kXaBytes);
                 bulk_g2s(s_xa + (size_t)xb * kXaBytes, p.XA + (size_t)tile * kXaBytes, kXaBytes, &bar_xa_full[xb]);
                 return true;
             };
-            bool ok = issue_xa(0);
-            int q = 0;
-            int64_t tt = 0;
-            for (int64_t i = 0; i < total_chunks && ok; ++i) {
-                if (q == 0 && tt + 1 < my_tiles) ok = issue_xa(tt + 1);
+            int64_t tile = u0 / nq, sg = 0;
+            int q = (int)(u0 % nq);
+            const int64_t last_tile = (u1 - 1) / nq;
+            bool ok = issue_xa(0, tile);
+            for (int64_t i = 0; i < total && ok; ++i) {
+                if ((i == 0 || q == 0) && tile < last_tile) ok = issue_xa(sg + 1, tile + 1);
                 const int s = (int)(i % kStages);
                 const int64_t u = i / kStages;
                 if (ok && u >= 1) ok = mbar_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1), &s_abort, p.err);
@@ -246,82 +263,89 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 bulk_g2s(dst + kXbBytes, p.DT + (size_t)q * kDtBytes, kDtBytes, &bar_stage_full[s]);
                 if (++q == nq) {
                     q = 0;
-                    ++tt;
+                    ++tile;
+                    ++sg;
                 }
             }
         }
     } else if (warp == kLoadWarp) {
         // ------------------------------------------------ distance MMA issuer
-        if (lane == 0 && my_tiles > 0 && nq > 0) {
+        if (lane == 0 && total > 0) {
             constexpr uint32_t idesc_d = instr_desc(0, kRows, kChunk);  // F16 x F16 -> F32, 128 x 128
             bool ok = true;
-            int64_t g = 0;
-            for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
-                const int xb = (int)(tt & 1);
-                ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((tt >> 1) & 1), &s_abort, p.err);
-                const uint32_t xa = smem_u32(s_xa + (size_t)xb * kXaBytes);
-                for (int q = 0; q < nq && ok; ++q, ++g) {
-                    const int s = (int)(g % kStages);
-                    const int buf = (int)(g % kBufs);
-                    const int64_t use = g / kBufs;
-                    ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err);
-                    if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err);
+            int64_t sg = -1;
+            int q = (int)(u0 % nq), xb = 0;
+            uint32_t xa = 0;
+            for (int64_t g = 0; g < total && ok; ++g) {
+                if (g == 0 || q == 0) {
+                    ++sg;
+                    xb = (int)(sg & 1);
+                    ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((sg >> 1) & 1), &s_abort, p.err);
+                    xa = smem_u32(s_xa + (size_t)xb * kXaBytes);
                     if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t xbs = smem_u32(s_stage + (size_t)s * kStageBytes);
-                    const uint32_t dS = tmem + (uint32_t)(kChunk * buf);
-                    for (int ks = 0; ks < KSTEPS_D; ++ks) {
-                        const uint32_t off = ks * 256;
-                        mma_ss(dS, smem_desc(xa + off, 128, kSboX), smem_desc(xbs + off, 128, kSboX), idesc_d,
-                               ks > 0 ? 1u : 0u);
-                    }
-                    tc_commit(&bar_s_full[buf]);
-                    if (q == nq - 1) tc_commit(&bar_xa_empty[xb]);
                 }
+                const int s = (int)(g % kStages);
+                const int buf = (int)(g % kBufs);
+                const int64_t use = g / kBufs;
+                ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err);
+                if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t xbs = smem_u32(s_stage + (size_t)s * kStageBytes);
+                const uint32_t dS = tmem + (uint32_t)(kChunk * buf);
+                for (int ks = 0; ks < KSTEPS_D; ++ks) {
+                    const uint32_t off = ks * 256;
+                    mma_ss(dS, smem_desc(xa + off, 128, kSboX), smem_desc(xbs + off, 128, kSboX), idesc_d,
+                           ks > 0 ? 1u : 0u);
+                }
+                tc_commit(&bar_s_full[buf]);
+                if (g == total - 1 || q == nq - 1) tc_commit(&bar_xa_empty[xb]);
+                if (++q == nq) q = 0;
             }
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ contraction MMA issuer
-        if (lane == 0 && my_tiles > 0 && nq > 0) {
+        if (lane == 0 && total > 0) {
             // BF16 x BF16 -> F32: 128 x 2C (P_hi against [Delta_hi; Delta_lo]) and 128 x C
             constexpr uint32_t idesc_c2 = instr_desc(1, kRows, 2 * C);
             constexpr uint32_t idesc_c = instr_desc(1, kRows, C);
             bool ok = true;
-            int64_t g = 0;
-            for (int64_t tt = 0; tt < my_tiles && ok; ++tt) {
-                for (int q = 0; q < nq && ok; ++q, ++g) {
-                    const int buf = (int)(g % kBufs);
-                    const int s = (int)(g % kStages);
-                    if (q == 0 && tt >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((tt - 1) & 1), &s_abort, p.err);
-                    if (!ok) break;
-                    // Delta^T of the stage: C rows of Delta_hi, then C rows of Delta_lo
-                    // (consecutive 8-row groups), so one N = 2C product gives hi*hi
-                    // and hi*lo side by side in accumulator columns [0, 2C)
-                    const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
-                    const uint32_t pb = tmem + (uint32_t)(kChunk * buf);
-                    const uint32_t a01 = tmem + kColAcc, a2 = a01 + 2 * C;
-                    // K-step ks: 16 BF16 values of P = 8 columns of P_hi at 16 ks and 8
-                    // of P_lo at 16 ks + 8; two 16-byte core columns of Delta^T (core
-                    // columns 128 B apart).  The K-steps of a column group start as
-                    // soon as its four transform warps have written their P.
+            int64_t sg = -1;
+            int q = (int)(u0 % nq);
+            for (int64_t g = 0; g < total && ok; ++g) {
+                const bool first = g == 0 || q == 0;
+                const int buf = (int)(g % kBufs);
+                const int s = (int)(g % kStages);
+                if (first && ++sg >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((sg - 1) & 1), &s_abort, p.err);
+                if (!ok) break;
+                // Delta^T of the stage: C rows of Delta_hi, then C rows of Delta_lo
+                // (consecutive 8-row groups), so one N = 2C product gives hi*hi
+                // and hi*lo side by side in accumulator columns [0, 2C)
+                const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
+                const uint32_t pb = tmem + (uint32_t)(kChunk * buf);
+                const uint32_t a01 = tmem + kColAcc, a2 = a01 + 2 * C;
+                // K-step ks: 16 BF16 values of P = 8 columns of P_hi at 16 ks and 8
+                // of P_lo at 16 ks + 8; two 16-byte core columns of Delta^T (core
+                // columns 128 B apart).  The K-steps of a column group start as
+                // soon as its four transform warps have written their P.
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS_C; ++ks) {
-                        if (ks % kUnits == 0) {
-                            ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
-                            if (!ok) break;
-                            tc_fence_after();
-                        }
-                        const uint32_t acc = (q == 0 && ks == 0) ? 0u : 1u;
-                        const uint32_t boff = ks * 256;
-                        const uint32_t pH = pb + 16u * ks, pL = pH + 8u;
-                        mma_ts(a01, pH, smem_desc(dth + boff, 128, kSboD), idesc_c2, acc);
-                        mma_ts(a2, pL, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
+                for (int ks = 0; ks < KSTEPS_C; ++ks) {
+                    if (ks % kUnits == 0) {
+                        ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
+                        if (!ok) break;
+                        tc_fence_after();
                     }
-                    if (!ok) break;
-                    tc_commit(&bar_buf_free[buf]);
-                    tc_commit(&bar_stage_empty[s]);
-                    if (q == nq - 1) tc_commit(&bar_acc_full);
+                    const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+                    const uint32_t boff = ks * 256;
+                    const uint32_t pH = pb + 16u * ks, pL = pH + 8u;
+                    mma_ts(a01, pH, smem_desc(dth + boff, 128, kSboD), idesc_c2, acc);
+                    mma_ts(a2, pL, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
                 }
+                if (!ok) break;
+                tc_commit(&bar_buf_free[buf]);
+                tc_commit(&bar_stage_empty[s]);
+                if (g == total - 1 || q == nq - 1) tc_commit(&bar_acc_full);
+                if (++q == nq) q = 0;
             }
         }
     } else {
@@ -332,47 +356,90 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         // cover the load latency).
         const int quarter = warp & 3, group = warp >> 2;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        const int total = (int)(my_tiles * nq);  // chunks of this CTA (< 2^31)
         bool ok = total > 0;
         // columns of unit (chunk c, unit h of this warp): S there is replaced by [P_hi | P_lo]
         auto u_addr = [&](int c, int h) -> uint32_t {
             return tmem + lane_base + (uint32_t)(kChunk * (c % kBufs) + kColsPerWarp * group + 16 * h);
         };
-        // tile epilogue (warps 0-3, one row per thread); it always passes both
-        // named barriers so that a failed wait cannot strand the other warps
-        auto epilogue = [&](int64_t tt) {
-            const int64_t tile = blockIdx.x + tt * gridDim.x;
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(tt & 1), &s_abort, p.err));
+        // Segment epilogue (warps 0-3, one row per thread).  A whole tile updates R
+        // from the accumulators; a tile shared with a neighbouring CTA first
+        // stores its part (part 0: chunks from the tile's start, part 1: the rest)
+        // in the boundary slot, and the second CTA to arrive updates R from
+        // part 0 + part 1, in that order whichever arrives last.  Every path passes
+        // the same named barriers so that a failed wait cannot strand the others.
+        auto epilogue = [&](int sg, int64_t tile, bool whole, int part) {
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(sg & 1), &s_abort, p.err));
             if (ok) tc_fence_after();
             const int64_t segi = tile / e.tiles_per_seg;
             const int64_t seg_lo = segi * e.seg;
             const int64_t seg_hi = min(seg_lo + e.seg, p.n);
-            const int64_t r0 = seg_lo + (tile % e.tiles_per_seg) * kRows;
-            const int64_t i = r0 + quarter * 32 + lane;
-            const bool live = ok && i < seg_hi;
+            const int row = quarter * 32 + lane;
+            const int64_t i = seg_lo + (tile % e.tiles_per_seg) * kRows + row;
             const bool diag = i >= col0 && i < col0 + ncols;
+            // the three partial products (hi*hi, hi*lo, lo*hi) of 16 columns
+            auto acc16 = [&](int c0, float (&a16)[16]) {
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + kColAcc + c0, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) a16[k] = __uint_as_float(r[k]);
+                tmem_ld16(tmem + lane_base + kColAcc + C + c0, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+                tmem_ld16(tmem + lane_base + kColAcc + 2 * C + c0, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+            };
+            bool apply = whole;
+            const int64_t bnd = part == 0 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - 1;
+            float* scr0 = p.scr + ((bnd * 2 + 0) * kRows + row) * C;
+            float* scr1 = p.scr + ((bnd * 2 + 1) * kRows + row) * C;
+            if (!whole) {
+                if (ok) {
+                    float* mine = part == 0 ? scr0 : scr1;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < C; c0 += 16) {
+                        float a16[16];
+                        acc16(c0, a16);
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4)
+                            __stcg(reinterpret_cast<float4*>(mine + c0 + k),
+                                   make_float4(a16[k], a16[k + 1], a16[k + 2], a16[k + 3]));
+                    }
+                    tc_fence_before();
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acc_free);
+                __threadfence();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (tid == 0) {
+                    int fin = 0;
+                    if (ok) {
+                        fin = atomicAdd(&p.tick[bnd], 1) == 1;
+                        if (fin) p.tick[bnd] = 0;  // both parts are in: ready for the next launch
+                        __threadfence();
+                    }
+                    s_fin = fin;
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                apply = s_fin != 0;
+            }
+            const bool live = ok && apply && i < seg_hi;
             // squares are summed in FP32 within a thread and a warp (at most 32 terms
             // each, relative error below 2e-6) and in FP64 beyond: FP64 arithmetic is
             // scarce on this part
             float sqf = 0.0f;
-            // 16 columns at a time: sum the three accumulators, update R, norms
+            // 16 columns at a time: the accumulated product, R update, norms
 #pragma unroll 1
             for (int c0 = 0; c0 < C; c0 += 16) {
                 float a16[16];
-                if (ok) {
-                    uint32_t r[16];
-                    tmem_ld16(tmem + lane_base + kColAcc + c0, r);
-                    tmem_wait_ld();
+                if (ok && whole) {
+                    acc16(c0, a16);
+                } else if (live) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) a16[k] = __uint_as_float(r[k]);
-                    tmem_ld16(tmem + lane_base + kColAcc + C + c0, r);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
-                    tmem_ld16(tmem + lane_base + kColAcc + 2 * C + c0, r);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+                    for (int k = 0; k < 16; ++k) a16[k] = __ldcg(scr0 + c0 + k) + __ldcg(scr1 + c0 + k);
                 }
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -384,21 +451,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                         p.R[i * C + c] = v;
                         sqf = fmaf(v, v, sqf);
                     }
-                    if (e.flags & kEpiColNorms) {
+                    if (apply && (e.flags & kEpiColNorms)) {
                         float w = v * v;
                         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
                         if (lane == 0) s_colred[warp][c0 + k] = (double)w;
                     }
                 }
             }
-            if (ok) tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_acc_free);
+            if (whole) {
+                if (ok) tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acc_free);
+            }
             double sq = sqf;
             for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
             if (lane == 0) red_d[warp] = sq;
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (tid == 0) {
+            if (tid == 0 && apply) {
                 e.part_norm[tile] = red_d[0] + red_d[1] + red_d[2] + red_d[3];
                 if (e.flags & kEpiColNorms)
                     for (int c = 0; c < C; ++c)
@@ -406,12 +475,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             }
             asm volatile("bar.sync 1, 128;" ::: "memory");
         };
-        int q_in_tile = 0;  // chunk index within the current tile
-        int64_t tile_no = 0;
+        // per-CTA counters fit in 32 bits (fewer registers in the hot loop)
+        int tile = (int)(u0 / (nq > 0 ? nq : 1)), sg = 0;
+        int q = nq > 0 ? (int)(u0 % nq) : 0, q_first = q;
+        const int ntot = (int)total;
         static_assert(kUnits == 2, "two units per warp and chunk");
         // one chunk: both 16-column units loaded together, transformed together,
         // stored in place; then signal the contraction MMA
-        for (int c = 0; c < total; ++c) {
+        for (int c = 0; c < ntot; ++c) {
             uint32_t ta[16], tb[16];
             if (ok)
                 ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[c % kBufs], (uint32_t)((c / kBufs) & 1),
@@ -443,10 +514,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             }
             __syncwarp();
             if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs][group]);
-            if (++q_in_tile == nq) {
-                if (warp < 4) epilogue(tile_no);
-                q_in_tile = 0;
-                ++tile_no;
+            if (c == ntot - 1 || q == nq - 1) {
+                const bool whole = q_first == 0 && q == nq - 1;
+                if (warp < 4) epilogue(sg, tile, whole, q_first == 0 ? 0 : 1);
+            }
+            if (++q == nq) {
+                q = 0;
+                q_first = 0;
+                ++tile;
+                ++sg;
             }
         }
     }
@@ -602,6 +678,7 @@ int tc_chunks_per_block(int64_t b) { return (int)((b + tc::kChunk - 1) / tc::kCh
 size_t tc_rows_bytes(int64_t ntiles, int kd) { return (size_t)ntiles * 128 * kd * 2; }
 size_t tc_cols_bytes(int64_t m, int cpb, int kd) { return (size_t)m * cpb * tc::kChunk * kd * 2; }
 size_t tc_delta_bytes(int cpb, int C) { return (size_t)cpb * 2 * C * tc::kChunk * 2; }
+size_t tc_share_bytes(int grid, int C) { return (size_t)grid * 2 * tc::kRows * C * sizeof(float); }
 
 cudaError_t launch_tc_pack_inputs(int kernel, const float* Xs, int64_t n, int d, int D, int64_t b, int64_t m,
                                   int64_t tps, int cpb, int kd, uint8_t* XA, uint8_t* XB, cudaStream_t st) {
@@ -648,6 +725,8 @@ cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int
     p.noise = l.noise;
     p.sel = l.sel;
     p.err = l.err;
+    p.scr = l.scr;
+    p.tick = l.tick;
     p.epi = l.epi;
     return launch_kmv_tc(kernel, p, C, grid, st);
 }

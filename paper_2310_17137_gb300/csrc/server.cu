@@ -68,6 +68,7 @@ size_t estimate_bytes(const ap_request& r) {
         bytes += ap::tc_rows_bytes(m * ((b + 127) / 128), kd);  // row operands
         bytes += ap::tc_cols_bytes(m, cpb, kd);                 // column operands
         bytes += ap::tc_delta_bytes(cpb, 16);                   // Delta^T
+        bytes += ap::tc_share_bytes(256, AP_MAX_RHS);           // boundary slots (up to 256 SMs)
     }
     bytes += (size_t)(M * D) * 4 + (size_t)(1 << 20);              // test inputs, partials
     const size_t ws_block = (size_t)(nt * 64) * (nt * 64) * 8 + (size_t)nt * 64 * 64 * 8;
