@@ -25,11 +25,13 @@
 // matches the all-FP64 factorisation (6e-16 vs 5e-16 on a Matern-5/2 block
 // with condition number 1.6e4, in a NumPy model of these exact steps).
 //
-// One CTA per 128 x 64 output super-tile (two row tiles i0, i0 + 1 against
-// one column tile j): bulk copies of the 8 slice planes of both operands
-// (192 KB of shared memory), 144 MMAs (36 slice products x 4 K-steps of 16)
-// into eight 64-column FP32 accumulators (all 512 tensor-memory columns), then
-// an epilogue of one row per thread.  Every wait is bounded.
+// Work item: a 128 x 64 output super-tile (two row tiles i0, i0 + 1 against
+// one column tile j) of one block: bulk copies of the 8 slice planes of both
+// operands (192 KB of shared memory), 144 MMAs (36 slice products x 4 K-steps
+// of 16) into eight 64-column FP32 accumulators (all 512 tensor-memory
+// columns), then an epilogue of one row per thread.  One persistent CTA per SM
+// walks the work items; the next item's slices are copied in while the
+// epilogue of the current one runs.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -133,33 +135,49 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* src0, int64
 // of tile k), written instead of subtracted.
 template <bool kTrsm>
 __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(double* A, int nt, int k, const uint8_t* S,
-                                                               size_t plane_bytes, const int* E, int* err) {
+                                                               size_t plane_bytes, const int* E, int* err,
+                                                               int tiles_per_block, int nwork) {
     extern __shared__ __align__(1024) uint8_t oz_smem[];
     __shared__ __align__(8) uint64_t bar_load, bar_mma;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ int s_ec[T];
-    const int z = blockIdx.y, tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int rem = nt - k - 1;
-    // super-tile (u, jj) of this CTA: row tiles i0 = k + 1 + 2u, i0 + 1 and
-    // column tile j = k + 1 + jj <= i0 + 1 (SYRK) or j = k (TRSM)
-    int u = 0, jj = (int)blockIdx.x;
-    if constexpr (kTrsm) {
-        u = jj;
-        jj = -1;
-    } else {
-        while (true) {
-            const int nc = min(2 * u + 2, rem);
-            if (jj < nc) break;
-            jj -= nc;
-            ++u;
-        }
-    }
-    const int i0 = k + 1 + 2 * u, j = k + 1 + jj;
     const int64_t ld = (int64_t)nt * T, rows_pad = ld + T;
-    const uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes;
     uint8_t* sA = oz_smem;
     uint8_t* sB = oz_smem + kSlices * kPlaneA;
+    // work item w = (block z, super-tile): row tiles i0 = k + 1 + 2u, i0 + 1 and
+    // column tile j = k + 1 + jj <= i0 + 1 (SYRK) or j = k (TRSM)
+    auto decode = [&](int w, int& z, int& i0, int& j) {
+        z = w / tiles_per_block;
+        int u = 0, jj = w - z * tiles_per_block;
+        if constexpr (kTrsm) {
+            u = jj;
+            jj = -1;
+        } else {
+            while (true) {
+                const int nc = min(2 * u + 2, rem);
+                if (jj < nc) break;
+                jj -= nc;
+                ++u;
+            }
+        }
+        i0 = k + 1 + 2 * u;
+        j = k + 1 + jj;
+    };
+    auto issue_loads = [&](int w) {
+        int z, i0, j;
+        decode(w, z, i0, j);
+        const uint8_t* Sz = S + (size_t)z * kSlices * plane_bytes;
+        mbar_expect_tx(&bar_load, kOzSmem);
+        for (int p = 0; p < kSlices; ++p)
+            bulk_g2s(sA + p * kPlaneA, Sz + (size_t)p * plane_bytes + (size_t)i0 * T * kRowBytes, kPlaneA,
+                     &bar_load);
+        for (int q = 0; q < kSlices; ++q)
+            bulk_g2s(sB + q * kPlaneB, Sz + (size_t)q * plane_bytes + (size_t)j * T * kRowBytes, kPlaneB,
+                     &bar_load);
+    };
 
     if (tid == 0) {
         mbar_init(&bar_load, 1);
@@ -173,96 +191,106 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(double* A, int n
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid < T) s_ec[tid] = E[(int64_t)z * rows_pad + (int64_t)j * T + tid];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    if (tid == 0 && (int)blockIdx.x < nwork) issue_loads((int)blockIdx.x);
 
-    if (tid == 0) {
-        mbar_expect_tx(&bar_load, kOzSmem);
-        for (int p = 0; p < kSlices; ++p)
-            bulk_g2s(sA + p * kPlaneA, Sz + (size_t)p * plane_bytes + (size_t)i0 * T * kRowBytes, kPlaneA,
-                     &bar_load);
-        for (int q = 0; q < kSlices; ++q)
-            bulk_g2s(sB + q * kPlaneB, Sz + (size_t)q * plane_bytes + (size_t)j * T * kRowBytes, kPlaneB,
-                     &bar_load);
-        if (mbar_wait(&bar_load, 0u, &s_abort, err)) {
-            tc_fence_after();
-            constexpr uint32_t idesc = instr_desc(1, kSlabRows, T);  // BF16 x BF16 -> F32, 128 x 64
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (int L = 2; L <= kSlices + 1; ++L) {
-                const uint32_t d = tmem + 64u * (uint32_t)(L - 2);
-                uint32_t acc = 0;
-                for (int p = max(1, L - kSlices); p <= min(kSlices, L - 1); ++p) {
-                    const int q = L - p;
-                    const uint32_t ap = a0 + (uint32_t)(p - 1) * kPlaneA, bq = b0 + (uint32_t)(q - 1) * kPlaneB;
+    // Persistent loop: the slices of the next work item are copied in while the
+    // epilogue of the current one runs (shared memory is free once its MMAs are
+    // done; the accumulators are free after the epilogue).
+    int it = 0;
+    for (int w = (int)blockIdx.x; w < nwork; w += (int)gridDim.x, ++it) {
+        int z, i0, j;
+        decode(w, z, i0, j);
+        if (tid < T) s_ec[tid] = E[(int64_t)z * rows_pad + (int64_t)j * T + tid];
+        __syncthreads();
+        if (tid == 0) {
+            if (mbar_wait(&bar_load, (uint32_t)(it & 1), &s_abort, err)) {
+                tc_fence_after();
+                constexpr uint32_t idesc = instr_desc(1, kSlabRows, T);  // BF16 x BF16 -> F32, 128 x 64
+                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+                for (int L = 2; L <= kSlices + 1; ++L) {
+                    const uint32_t d = tmem + 64u * (uint32_t)(L - 2);
+                    uint32_t acc = 0;
+                    for (int p = max(1, L - kSlices); p <= min(kSlices, L - 1); ++p) {
+                        const int q = L - p;
+                        const uint32_t ap = a0 + (uint32_t)(p - 1) * kPlaneA, bq = b0 + (uint32_t)(q - 1) * kPlaneB;
 #pragma unroll
-                    for (int ks = 0; ks < T / 16; ++ks) {
-                        mma_ss(d, smem_desc(ap + ks * 256, 128, 1024), smem_desc(bq + ks * 256, 128, 1024), idesc,
-                               acc);
-                        acc = 1;
+                        for (int ks = 0; ks < T / 16; ++ks) {
+                            mma_ss(d, smem_desc(ap + ks * 256, 128, 1024), smem_desc(bq + ks * 256, 128, 1024),
+                                   idesc, acc);
+                            acc = 1;
+                        }
                     }
                 }
+                tc_commit(&bar_mma);
             }
-            tc_commit(&bar_mma);
         }
-    }
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, 0u, &s_abort, err));
-    if (ok) tc_fence_after();
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_mma, (uint32_t)(it & 1), &s_abort, err));
+        if (ok) tc_fence_after();
+        // the shared slices are consumed: fetch the next work item's
+        if (tid == 0 && ok && w + (int)gridDim.x < nwork) issue_loads(w + (int)gridDim.x);
 
-    // epilogue: warp w owns tensor-memory lanes (rows) 32 (w % 4) .. + 31 and
-    // columns 32 (w / 4) .. + 31 of the super-tile
-    const int rl = 32 * (warp & 3) + (tid & 31);
-    const int64_t r = (int64_t)i0 * T + rl;
-    const int rtile = i0 + rl / T;
-    const bool live = ok && rtile < nt && (kTrsm || j <= rtile);
-    const int er = live ? E[(int64_t)z * rows_pad + r] : 0;
-    double* Crow = A + (int64_t)z * ld * ld + r * ld + (int64_t)j * T;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    // exact conversions: an FP32 integer below 2^22 through the FP32 mantissa,
-    // a 64-bit integer below 2^51 through the FP64 mantissa
-    constexpr float kMagicF = 12582912.0f;                  // 1.5 * 2^23
-    constexpr long long kMagicDBits = 0x4338000000000000LL;  // 1.5 * 2^52
-    constexpr double kMagicD = 6755399441055744.0;
+        // epilogue: warp v owns tensor-memory lanes (rows) 32 (v % 4) .. + 31 and
+        // columns 32 (v / 4) .. + 31 of the super-tile
+        const int rl = 32 * (warp & 3) + (tid & 31);
+        const int64_t r = (int64_t)i0 * T + rl;
+        const int rtile = i0 + rl / T;
+        const bool live = ok && rtile < nt && (kTrsm || j <= rtile);
+        const int er = live ? E[(int64_t)z * rows_pad + r] : 0;
+        double* Crow = A + (int64_t)z * ld * ld + r * ld + (int64_t)j * T;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        // exact conversions: an FP32 integer below 2^22 through the FP32 mantissa,
+        // a 64-bit integer below 2^51 through the FP64 mantissa
+        constexpr float kMagicF = 12582912.0f;                  // 1.5 * 2^23
+        constexpr long long kMagicDBits = 0x4338000000000000LL;  // 1.5 * 2^52
+        constexpr double kMagicD = 6755399441055744.0;
 #pragma unroll 1
-    for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32; c0 += 16) {
-        long long H[16], Lo[16];
+        for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32; c0 += 16) {
+            long long H[16], Lo[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) H[c] = Lo[c] = 0;
+            for (int c = 0; c < 16; ++c) H[c] = Lo[c] = 0;
 #pragma unroll
-        for (int L = 2; L <= kSlices + 1; ++L) {
-            uint32_t v[16];
-            if (ok) {
-                tmem_ld16(tmem + lane_base + 64u * (uint32_t)(L - 2) + (uint32_t)c0, v);
-                tmem_wait_ld();
-            } else {
+            for (int L = 2; L <= kSlices + 1; ++L) {
+                uint32_t v[16];
+                if (ok) {
+                    tmem_ld16(tmem + lane_base + 64u * (uint32_t)(L - 2) + (uint32_t)c0, v);
+                    tmem_wait_ld();
+                } else {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) v[c] = 0u;
+                    for (int c = 0; c < 16; ++c) v[c] = 0u;
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const long long iv =
+                        (long long)(__float_as_int(__uint_as_float(v[c]) + kMagicF) - __float_as_int(kMagicF));
+                    if (L <= 5) H[c] = H[c] * 128 + iv;
+                    else Lo[c] = Lo[c] * 128 + iv;
+                }
             }
+            if (live) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const long long iv =
-                    (long long)(__float_as_int(__uint_as_float(v[c]) + kMagicF) - __float_as_int(kMagicF));
-                if (L <= 5) H[c] = H[c] * 128 + iv;
-                else Lo[c] = Lo[c] * 128 + iv;
+                for (int c = 0; c < 16; ++c) {
+                    const double hd = __longlong_as_double(kMagicDBits + H[c]) - kMagicD;
+                    const double ld_ = __longlong_as_double(kMagicDBits + Lo[c]) - kMagicD;
+                    const double t = fma(ld_, 0x1p-28, hd);
+                    const int ec = s_ec[c0 + c];
+                    const int e = er + ec - 35;
+                    double scale;
+                    if (e >= -1022 && e <= 1023) scale = __longlong_as_double((long long)(e + 1023) << 52);
+                    else scale = ldexp(1.0, max(-1074, min(1023, e)));
+                    const double nv = kTrsm ? t * scale : fma(-t, scale, Crow[c0 + c]);
+                    Crow[c0 + c] = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000LL) : nv;
+                }
             }
         }
-        if (live) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const double hd = __longlong_as_double(kMagicDBits + H[c]) - kMagicD;
-                const double ld_ = __longlong_as_double(kMagicDBits + Lo[c]) - kMagicD;
-                const double t = fma(ld_, 0x1p-28, hd);
-                const int ec = s_ec[c0 + c];
-                const int e = er + ec - 35;
-                double scale;
-                if (e >= -1022 && e <= 1023) scale = __longlong_as_double((long long)(e + 1023) << 52);
-                else scale = ldexp(1.0, max(-1074, min(1023, e)));
-                const double nv = kTrsm ? t * scale : fma(-t, scale, Crow[c0 + c]);
-                Crow[c0 + c] = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000LL) : nv;
-            }
-        }
+        // every accumulator has been read before the next MMAs overwrite them
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (s_abort) break;
     }
 
     tc_fence_before();
@@ -277,6 +305,21 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(double* A, int n
         }
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
+}
+
+// persistent grid: one CTA per SM (the slice planes fill shared memory)
+int sm_count() {
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            sms = v;
+        else
+            sms = 148;
+        cudaGetLastError();
+    }
+    return sms;
 }
 
 }  // namespace
@@ -299,9 +342,11 @@ cudaError_t launch_oz_update(double* A, int nt, int k, int g, uint8_t* S, int* E
     oz_slice_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)g), 256, 0, st>>>(
         A + (int64_t)(k + 1) * T * ld + (int64_t)k * T, ld * ld, ld, rows, (int64_t)(k + 1) * T, ld + T, pb, S, E);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    int64_t tiles = 0;
+    int tiles = 0;
     for (int u = 0; 2 * u < rem; ++u) tiles += std::min(2 * u + 2, rem);
-    oz_gemm_kernel<false><<<dim3((unsigned)tiles, (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err);
+    const int nwork = tiles * g;
+    oz_gemm_kernel<false><<<(unsigned)std::min(nwork, sm_count()), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err,
+                                                                                            tiles, nwork);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
@@ -323,8 +368,9 @@ cudaError_t launch_oz_trsm(double* A, const double* Dinv, int nt, int k, int g, 
     oz_slice_kernel<<<dim3(T / 32, (unsigned)g), 256, 0, st>>>(Dinv + (int64_t)k * T * T, (int64_t)nt * T * T, T,
                                                                 T, (int64_t)k * T, ld + T, pb, S, E);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    oz_gemm_kernel<true><<<dim3((unsigned)((rem + 1) / 2), (unsigned)g), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb,
-                                                                                                    E, err);
+    const int tiles = (rem + 1) / 2, nwork = tiles * g;
+    oz_gemm_kernel<true><<<(unsigned)std::min(nwork, sm_count()), kOzThreads, kOzSmem, st>>>(A, nt, k, S, pb, E, err,
+                                                                                           tiles, nwork);
     if (launches) *launches += 3;
     return cudaGetLastError();
 }
