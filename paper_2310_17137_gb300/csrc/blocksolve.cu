@@ -293,7 +293,7 @@ cudaError_t launch_solve_inst(const SolveParams& p, cudaStream_t st) {
 }  // namespace
 
 void block_solve_layout(int nt, int num_sms, int* tpc, int* maxj) {
-    const int64_t target = 4LL * std::max(1, num_sms);
+    const int64_t target = 8LL * std::max(1, num_sms);
     *tpc = (int)std::max<int64_t>(1, (solve_ntri(nt) + target - 1) / target);
     *maxj = (nt + *tpc - 1) / *tpc + 1;
 }
