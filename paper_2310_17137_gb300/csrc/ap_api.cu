@@ -253,7 +253,10 @@ ap_status build_cache(ap_ctx* ctx) {
     const bool emulate = ctx->o.cache_gemm == AP_CACHE_TC_EXACT;
     const size_t per_block = (size_t)(edge * edge + ctx->nt * tile_elems) * sizeof(double) +
                              (emulate ? oz_slice_bytes(ctx->nt) + oz_expo_ints(ctx->nt) * sizeof(int) : 0);
-    size_t cap = (size_t)8 << 30;
+    // FP64 workspace of at most 16 GiB (or what the HBM budget leaves): as many
+    // blocks per group as fit, the groups of equal size (every group pays the
+    // same chain of dependent launches, however few blocks it holds)
+    size_t cap = (size_t)16 << 30;
     if (ctx->o.hbm_budget) {
         const size_t left = ctx->o.hbm_budget > ctx->bytes ? ctx->o.hbm_budget - ctx->bytes : 0;
         cap = std::min(cap, left);
@@ -262,6 +265,8 @@ ap_status build_cache(ap_ctx* ctx) {
     if (g < 1) return AP_ERR_NOMEM;
     g = std::min<int64_t>(g, ctx->m);
     g = std::min<int64_t>(g, 65535);
+    const int64_t ngroups = (ctx->m + g - 1) / g;
+    g = (ctx->m + ngroups - 1) / ngroups;
     double* A = nullptr;
     double* Dinv = nullptr;
     AP_TRY(dalloc_t(ctx, &A, (size_t)(g * edge * edge)));
