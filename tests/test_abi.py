@@ -64,6 +64,11 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         _capi.AP_ERR_INVALID_ARG
     assert lib.ap_solve(None, None, 1, None, None, None) == _capi.AP_ERR_INVALID_ARG
     lib.ap_destroy(None)
+    # the cache's FP64 kernel values: unknown kernel, negative count or NULL arrays
+    assert lib.ap_phi_fp64_eval(7, None, 1, None) == _capi.AP_ERR_INVALID_ARG
+    assert lib.ap_phi_fp64_eval(0, None, -1, None) == _capi.AP_ERR_INVALID_ARG
+    assert lib.ap_phi_fp64_eval(0, None, 3, None) == _capi.AP_ERR_INVALID_ARG
+    assert lib.ap_phi_fp64_eval(2, None, 0, None) == _capi.AP_OK
 
 
 def test_package_has_no_cpu_fallback():
