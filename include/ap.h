@@ -23,6 +23,9 @@
  *   - Errors come back as ap_status codes; nothing exits, traps or prints.
  *     After AP_ERR_CUDA the context should be destroyed.
  *   - A context is not thread safe: one call at a time per context.
+ *   - A context belongs to the device that was current at ap_create.  Every
+ *     call makes that device current for its duration and restores the
+ *     caller's current device before it returns.
  */
 #ifndef AP_H
 #define AP_H
@@ -47,7 +50,8 @@ typedef enum {
     AP_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (serving workers) */
     AP_ERR_CUDA = 7,          /* a CUDA runtime call failed */
     AP_ERR_UNSUPPORTED = 8,   /* option combination not built */
-    AP_ERR_SCRATCH_LIMIT = 9  /* ap_grad_quadforms_static: problem exceeds the fixed scratch */
+    AP_ERR_SCRATCH_LIMIT = 9, /* ap_grad_quadforms_static: problem exceeds the fixed scratch */
+    AP_ERR_CANCELLED = 10     /* the caller's cancel flag was set (checked between epochs) */
 } ap_status;
 
 /* Kernel family, Sec. 5 ("Datasets and Models") and App. E (Matern nu = 1.5):
@@ -131,6 +135,12 @@ typedef struct ap_opts {
     int32_t profile;      /* 1: time every block solve and residual update with CUDA events */
     int32_t residual_mode; /* ap_residual_mode: arithmetic of the residual recompute */
     int32_t cache_gemm;   /* ap_cache_gemm: arithmetic of the Cholesky trailing updates */
+    int64_t wait_limit_cycles; /* bound of each device-side wait of the tensor-core update, in SM
+                                  clock cycles; <= 0: about 2 s.  A wait that runs out ends the
+                                  kernel early and the call returns AP_ERR_TIMEOUT */
+    const volatile int32_t* cancel; /* optional host flag: when it reads non-zero at the end of an
+                                       epoch, ap_solve / ap_mll_grad stop with AP_ERR_CANCELLED
+                                       (W holds the last iterate) */
 } ap_opts;
 
 /* Report of ap_solve / ap_mll_grad.  rel_res_* hold the first c columns. */
@@ -167,7 +177,8 @@ void ap_opts_default(ap_opts* o);
  * setting; Table 6: (1/3) n b^2 flops, n b memory).  The factorisation runs in
  * FP64; the factor's inverse L_I^{-1} is stored in FP32.
  * Errors: INVALID_ARG (n < 1, d not in [1, 32], block < 1, bad hyper),
- * NOMEM, NOT_SPD (no context is returned), CUDA. */
+ * NAN (a NaN or Inf in X), NOMEM, NOT_SPD, TIMEOUT, CUDA; no context is
+ * returned on error. */
 ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d,
                     const ap_hyper* h, const ap_opts* o);
 
@@ -179,7 +190,9 @@ ap_status ap_set_hyper(ap_ctx* ctx, const ap_hyper* h);
  * first recomputed as B - K_hat W0 (warm start / resume).  W_dev (n x c) gets
  * the result.  info (may be NULL) gets the report.
  * Returns OK when the stopping rule held after >= min_epochs epochs,
- * NOT_CONVERGED at max_epochs / max_steps (W still written), NAN, CUDA. */
+ * NOT_CONVERGED at max_epochs / max_steps (W still written), NAN (a NaN or Inf
+ * in the residual, e.g. from B), CANCELLED (opts.cancel), TIMEOUT (a bounded
+ * device wait of the tensor-core update ran out), CUDA. */
 ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_dev,
                    float* W_dev, ap_info* info);
 
@@ -191,7 +204,8 @@ ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W
 
 /* Posterior mean (Sec. 2): mean_dev[t] = mu + s * sum_j phi(x*_t, x_j) w_j for
  * the M test inputs Xs_dev (device, M x d).  w_dev (device, n) is
- * K_hat^{-1} (y - mu), e.g. column 0 of ap_solve's W.  No noise term. */
+ * K_hat^{-1} (y - mu), e.g. column 0 of ap_solve's W.  No noise term.
+ * AP_ERR_NAN (means still written) when a test input is NaN or Inf. */
 ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, int64_t M,
                           float* mean_dev);
 
@@ -208,13 +222,16 @@ ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev,
 #define AP_STATIC_SCRATCH_BYTES (1u << 20)
 
 /* ap_grad_quadforms without any device allocation.  The paper has no
- * counterpart: this entry point exists for callers that must not allocate in
- * their steady state -- code running while a CUDA stream is being captured
- * into a graph, latency-bound serving loops (cudaMalloc and cudaFree
- * synchronise the whole device), and processes whose memory pool already owns
- * the free HBM.  Such a caller creates the context once at set-up (ap_create
- * allocates) and then calls this function, which calls no cudaMalloc, no
- * cudaFree and no allocating library routine.
+ * counterpart.  Some callers cannot let a library allocate device memory once
+ * their steady state has begun:
+ *   - latency-bound serving loops: cudaMalloc and cudaFree synchronise the
+ *     whole device, stalling every other stream in flight;
+ *   - processes whose own memory pool (an inference server's arena, a
+ *     framework's caching allocator) has already reserved the free HBM, so
+ *     that a further cudaMalloc fails.
+ * Such a caller creates the context once at set-up (ap_create allocates) and
+ * then calls this function, which calls no cudaMalloc, no cudaFree and no
+ * allocating library routine.
  *   - Same result as ap_grad_quadforms (same kernel; only the order in which
  *     the per-CTA partial sums are added may differ).
  *   - c must be 1, 4, 16 or 32: U_dev and V_dev (n x c, device) are read in
@@ -227,9 +244,11 @@ ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev,
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
- *   - Work runs on the context's stream (opts.stream) and the call returns
- *     when out_host is written.  Calls that overlap on the GPU (from several
- *     threads or streams) share the scratch and race: serialise them. */
+ *   - Work runs on the context's stream (opts.stream); the call copies the
+ *     sums to the host and synchronises that stream before it returns.  The
+ *     array keeps the last call's contents; each call clears what must start
+ *     at zero.  Calls that overlap on the GPU (from several threads or
+ *     streams) share the array and race: serialise them. */
 ap_status ap_grad_quadforms_static(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c,
                                    const double* alpha_host, double* out_host);
 
@@ -242,8 +261,28 @@ ap_status ap_grad_quadforms_static(ap_ctx* ctx, const float* U_dev, const float*
 ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const float* Z_dev,
                       float* grad_host, ap_info* info);
 
+/* The residual R that Alg. 1 tracked (Eq. text_update_of_r) as the last
+ * ap_solve left it: after the last inner step, or after the last FP32
+ * recompute when that solve refined or certified (low-precision forms, and
+ * the stopping rule).  R_dev (device, n x c) gets it; c must equal the last
+ * solve's c.  A verification aid: comparing it with B - K_hat W of the
+ * returned W shows the accumulated error of the residual updates.
+ * The solve inside ap_mll_grad counts as a solve.  AP_ERR_INVALID_ARG when no
+ * solve has left a residual (none yet, a later ap_residual overwrote it, or a
+ * call with another padded width resized the buffers) or c differs;
+ * AP_ERR_CUDA. */
+ap_status ap_tracked_residual(ap_ctx* ctx, int32_t c, float* R_dev);
+
+/* The cudaError_t value of the CUDA call behind this context's last
+ * AP_ERR_CUDA (0 if there was none), for diagnostics; 0 for NULL. */
+int32_t ap_last_cuda_error(const ap_ctx* ctx);
+
 /* Number of kernels this context has launched since ap_create (all calls). */
 int64_t ap_launch_count(const ap_ctx* ctx);
+
+/* Bytes of device memory the context holds right now (scaled inputs, the
+ * Cholesky cache, work buffers); 0 for NULL. */
+size_t ap_device_bytes(const ap_ctx* ctx);
 
 /* Measured SFU throughput of the current device, in results per SM clock, of
  * the two operations kernel evaluation is made of: ex2.approx (every kernel)
@@ -306,6 +345,7 @@ typedef struct ap_request_result {
     double queue_s;           /* submit -> start */
     double latency_s;         /* submit -> result written */
     size_t reserved_bytes;    /* HBM reserved for the request while it runs */
+    int32_t started;          /* 1 once a worker has taken the request */
 } ap_request_result;
 
 /* Start a server on device `device` with `slots` worker streams and an HBM
@@ -317,6 +357,12 @@ ap_status ap_server_submit(ap_server* srv, const ap_request* req, int64_t* id);
 ap_status ap_server_poll(ap_server* srv, int64_t id, ap_request_result* res);
 /* Wait up to timeout_s seconds for a request; TIMEOUT if it is not done. */
 ap_status ap_server_wait(ap_server* srv, int64_t id, double timeout_s, ap_request_result* res);
+/* Cancel a request.  A request not yet started is dropped; a running one
+ * stops at the end of its current epoch.  Either way it finishes with status
+ * AP_ERR_CANCELLED and writes no posterior mean.  Other requests are not
+ * affected.  A request already done keeps its result.  INVALID_ARG for an
+ * unknown id. */
+ap_status ap_server_cancel(ap_server* srv, int64_t id);
 /* Finish admitted requests, drop the rest, stop the workers. */
 void ap_server_destroy(ap_server* srv);
 

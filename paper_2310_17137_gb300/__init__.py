@@ -19,7 +19,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _capi
-from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_INVALID_ARG, AP_ERR_NAN, AP_ERR_NOMEM,  # noqa: F401
+from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_ERR_CANCELLED, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_INVALID_ARG, AP_ERR_NAN, AP_ERR_NOMEM,  # noqa: F401
                     AP_ERR_NOT_CONVERGED, AP_ERR_NOT_SPD, AP_ERR_TIMEOUT, AP_ERR_UNSUPPORTED,
                     AP_FP16_REFINE, AP_FP32, AP_MATERN32, AP_MATERN52, AP_OK, AP_RBF, AP_SEL_CYCLIC,
                     AP_SEL_GS, AP_SEL_RANDOM, AP_STOP_FRO, AP_STOP_MAX_REL, AP_STOP_MEAN_REL,
@@ -28,12 +28,18 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_BF16_REFINE, AP_ERR_CUDA, AP_ERR_IN
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ApServer", "MLLDataFit"]
+           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ap_tracked_residual", "ap_device_bytes", "ApServer",
+           "MLLDataFit"]
 
 
 class ApError(RuntimeError):
-    def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {ap_status_str(status)}")
+    def __init__(self, status: int, where: str, ctx=None):
+        msg = f"{where}: {ap_status_str(status)}"
+        self.cuda_error = 0
+        if ctx is not None and status == AP_ERR_CUDA:
+            self.cuda_error = int(_capi.load().ap_last_cuda_error(ctx.handle))
+            msg += f" (cudaError_t {self.cuda_error})"
+        super().__init__(msg)
         self.status = status
 
 
@@ -123,7 +129,7 @@ def ap_set_hyper(ctx: Context, hyper: Hyper) -> None:
     h, ell = hyper.to_c()
     st = _capi.load().ap_set_hyper(ctx.handle, ctypes.byref(h))
     if st != AP_OK:
-        raise ApError(st, "ap_set_hyper")
+        raise ApError(st, "ap_set_hyper", ctx)
 
 
 def info_dict(info: _capi.ap_info) -> dict:
@@ -146,7 +152,7 @@ def ap_solve(ctx: Context, B, W0=None, W=None):
     info = _capi.ap_info()
     st = _capi.load().ap_solve(ctx.handle, _ptr(B2), c, _ptr(W0), _ptr(W), ctypes.byref(info))
     if st not in (AP_OK, AP_ERR_NOT_CONVERGED):
-        raise ApError(st, "ap_solve")
+        raise ApError(st, "ap_solve", ctx)
     trace = None
     if ctx._trace is not None:
         trace = np.frombuffer(ctx._trace, dtype=np.int32)[:min(info.steps, ctx.opts.trace_cap)].copy()
@@ -162,7 +168,7 @@ def ap_residual(ctx: Context, B, W, R=None):
         R = torch.empty_like(B2)
     st = _capi.load().ap_residual(ctx.handle, _ptr(B2), B2.shape[1], _ptr(W2), _ptr(R))
     if st != AP_OK:
-        raise ApError(st, "ap_residual")
+        raise ApError(st, "ap_residual", ctx)
     return R
 
 
@@ -173,7 +179,7 @@ def ap_predict_mean(ctx: Context, w, Xs, out=None):
         out = torch.empty(Xs.shape[0], device=Xs.device, dtype=torch.float32)
     st = _capi.load().ap_predict_mean(ctx.handle, _ptr(w), _ptr(Xs), Xs.shape[0], _ptr(out))
     if st != AP_OK:
-        raise ApError(st, "ap_predict_mean")
+        raise ApError(st, "ap_predict_mean", ctx)
     return out
 
 
@@ -186,14 +192,15 @@ def ap_grad_quadforms(ctx: Context, U, V, alpha) -> np.ndarray:
     st = _capi.load().ap_grad_quadforms(ctx.handle, _ptr(U2), _ptr(V2), U2.shape[1], a.ctypes.data,
                                         out.ctypes.data)
     if st != AP_OK:
-        raise ApError(st, "ap_grad_quadforms")
+        raise ApError(st, "ap_grad_quadforms", ctx)
     return out
 
 
 def ap_grad_quadforms_static(ctx: Context, U, V, alpha) -> np.ndarray:
-    """ap_grad_quadforms without device allocation (fixed scratch inside libap.so);
-    for callers that may not allocate in their steady state.  c must be 1, 4,
-    16 or 32; overlapping calls share the scratch and must be serialised."""
+    """ap_grad_quadforms without device allocation (fixed scratch inside libap.so),
+    for callers that may not allocate once their steady state has begun (serving
+    loops, processes whose own pool holds the free HBM).  c must be 1, 4, 16 or
+    32; overlapping calls share the scratch and must be serialised."""
     U2 = U if U.dim() == 2 else U.reshape(-1, 1)
     V2 = V if V.dim() == 2 else V.reshape(-1, 1)
     a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
@@ -201,7 +208,7 @@ def ap_grad_quadforms_static(ctx: Context, U, V, alpha) -> np.ndarray:
     st = _capi.load().ap_grad_quadforms_static(ctx.handle, _ptr(U2), _ptr(V2), U2.shape[1], a.ctypes.data,
                                                out.ctypes.data)
     if st != AP_OK:
-        raise ApError(st, "ap_grad_quadforms_static")
+        raise ApError(st, "ap_grad_quadforms_static", ctx)
     return out
 
 
@@ -212,12 +219,28 @@ def ap_mll_grad(ctx: Context, y, n_probes: int, Z=None):
     info = _capi.ap_info()
     st = _capi.load().ap_mll_grad(ctx.handle, _ptr(y), int(n_probes), _ptr(Z), g.ctypes.data, ctypes.byref(info))
     if st not in (AP_OK, AP_ERR_NOT_CONVERGED):
-        raise ApError(st, "ap_mll_grad")
+        raise ApError(st, "ap_mll_grad", ctx)
     return st, g, info_dict(info)
 
 
 def ap_launch_count(ctx: Context) -> int:
     return int(_capi.load().ap_launch_count(ctx.handle))
+
+
+def ap_device_bytes(ctx: Context) -> int:
+    """Device bytes the context holds right now."""
+    return int(_capi.load().ap_device_bytes(ctx.handle))
+
+
+def ap_tracked_residual(ctx: Context, c: int, R=None):
+    """The residual the last solve tracked (n x c), for verification."""
+    torch = _torch()
+    if R is None:
+        R = torch.empty((ctx.n, c), dtype=torch.float32, device=ctx.X.device)
+    st = _capi.load().ap_tracked_residual(ctx.handle, c, _ptr(R))
+    if st != AP_OK:
+        raise ApError(st, "ap_tracked_residual", ctx)
+    return R
 
 
 def ap_sfu_rates() -> tuple:
@@ -280,7 +303,14 @@ class ApServer:
     @staticmethod
     def _res(res) -> dict:
         return dict(done=bool(res.done), status=res.status, epochs=res.epochs, rel_res=res.rel_res,
-                    queue_s=res.queue_s, latency_s=res.latency_s, reserved_bytes=res.reserved_bytes)
+                    queue_s=res.queue_s, latency_s=res.latency_s, reserved_bytes=res.reserved_bytes,
+                    started=bool(res.started))
+
+    def cancel(self, rid: int) -> None:
+        """Drop a queued request, or stop a running one at the end of its epoch."""
+        st = self.L.ap_server_cancel(self.handle, int(rid))
+        if st != AP_OK:
+            raise ApError(st, "ap_server_cancel")
 
     def poll(self, rid: int) -> dict:
         res = _capi.ap_request_result()

@@ -13,6 +13,7 @@ AP_MAX_DIM = 32
 AP_OK, AP_ERR_INVALID_ARG, AP_ERR_NOMEM, AP_ERR_NOT_SPD, AP_ERR_NAN = 0, 1, 2, 3, 4
 AP_ERR_NOT_CONVERGED, AP_ERR_TIMEOUT, AP_ERR_CUDA, AP_ERR_UNSUPPORTED = 5, 6, 7, 8
 AP_ERR_SCRATCH_LIMIT = 9
+AP_ERR_CANCELLED = 10
 AP_STATIC_SCRATCH_BYTES = 1 << 20
 AP_RBF, AP_MATERN32, AP_MATERN52 = 0, 1, 2
 AP_FP32, AP_BF16_REFINE, AP_FP16_REFINE = 0, 1, 2
@@ -26,7 +27,8 @@ EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_resid
            "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy", "ap_status_str",
            "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval",
            "ap_grad_quadforms_static", "ap_server_create", "ap_server_submit", "ap_server_poll",
-           "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result"]
+           "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result",
+           "ap_tracked_residual", "ap_device_bytes", "ap_last_cuda_error", "ap_server_cancel"]
 
 
 class ap_hyper(ctypes.Structure):
@@ -41,7 +43,8 @@ class ap_opts(ctypes.Structure):
                 ("refine_every", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("hbm_budget", ctypes.c_size_t), ("block_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_cap", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("residual_mode", ctypes.c_int32), ("cache_gemm", ctypes.c_int32)]
+                ("residual_mode", ctypes.c_int32), ("cache_gemm", ctypes.c_int32),
+                ("wait_limit_cycles", ctypes.c_int64), ("cancel", ctypes.c_void_p)]
 
 
 class ap_info(ctypes.Structure):
@@ -67,7 +70,7 @@ class ap_request(ctypes.Structure):
 class ap_request_result(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int), ("epochs", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double),
-                ("reserved_bytes", ctypes.c_size_t)]
+                ("reserved_bytes", ctypes.c_size_t), ("started", ctypes.c_int32)]
 
 
 _lib = None
@@ -102,6 +105,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_mll_grad": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
         "ap_destroy": (None, [P]),
         "ap_launch_count": (i64, [P]),
+        "ap_device_bytes": (ctypes.c_size_t, [P]),
+        "ap_last_cuda_error": (i32, [P]),
+        "ap_tracked_residual": (st, [P, i32, P]),
         "ap_sfu_rates": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "ap_phi_fp64_eval": (st, [i32, P, i64, P]),
         "ap_server_create": (st, [ctypes.POINTER(P), ctypes.c_size_t, i32, i32]),
@@ -109,6 +115,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_server_poll": (st, [P, i64, ctypes.POINTER(ap_request_result)]),
         "ap_server_wait": (st, [P, i64, ctypes.c_double, ctypes.POINTER(ap_request_result)]),
         "ap_server_destroy": (None, [P]),
+        "ap_server_cancel": (st, [P, i64]),
         "ap_status_str": (ctypes.c_char_p, [st]),
         "ap_sizeof_opts": (ctypes.c_size_t, []),
         "ap_sizeof_info": (ctypes.c_size_t, []),

@@ -18,6 +18,7 @@
 using namespace ap;
 
 struct ap_ctx {
+    int device = 0;  // current device at ap_create; every call runs with it current
     int64_t n = 0;
     int d = 0, D = 0;
     const float* X = nullptr;
@@ -74,6 +75,7 @@ struct ap_ctx {
     int* tc_tick = nullptr;
     int* tc_err = nullptr;
     int64_t launches = 0;
+    int r_tracked_c = 0;  // c of the solve whose residual R holds (0: none)
     cudaError_t last_cuda = cudaSuccess;
 };
 
@@ -88,6 +90,10 @@ namespace {
             return AP_ERR_CUDA;                           \
         }                                                 \
     } while (0)
+
+#define AP_DEVICE_GUARD(ctx)               \
+    DeviceGuard _dg((ctx)->device);        \
+    if (!_dg.ok()) return AP_ERR_CUDA
 
 #define AP_TRY(expr)                       \
     do {                                   \
@@ -228,7 +234,7 @@ ap_status prep_inputs(ap_ctx* ctx, const float* X, int64_t n, float* out, float*
         sh[k] = (float)sc;
         sl[k] = (float)(sc - (double)sh[k]);
     }
-    AP_CK(launch_prep_inputs(X, n, ctx->d, ctx->D, sh, sl, out, out_lo, ctx->st));
+    AP_CK(launch_prep_inputs(X, n, ctx->d, ctx->D, sh, sl, out, out_lo, ctx->nan_flag, ctx->st));
     ++ctx->launches;
     return AP_OK;
 }
@@ -241,6 +247,7 @@ bool use_compensated(const ap_ctx* ctx) {
 
 ap_status build_cache(ap_ctx* ctx) {
     drop_graph(ctx);
+    AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
     AP_TRY(prep_inputs(ctx, ctx->X, ctx->n, ctx->Xs, ctx->Xs_lo));
     if (ctx->tc) {
         AP_CK(launch_tc_pack_inputs(ctx->kernel, ctx->Xs, ctx->n, ctx->d, ctx->D, ctx->b, ctx->m, ctx->tps128, ctx->cpb, ctx->kd,
@@ -317,8 +324,10 @@ ap_status build_cache(ap_ctx* ctx) {
     dfree(ctx, Dinv);
     dfree(ctx, ozS);
     dfree(ctx, ozE);
-    int tmo = 0;
+    int tmo = 0, nanx = 0;
     AP_CK(cudaMemcpy(&tmo, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    AP_CK(cudaMemcpy(&nanx, ctx->nan_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (nanx) return AP_ERR_NAN;  // a NaN or Inf training input
     if (tmo) return AP_ERR_TIMEOUT;
     std::vector<int> bad((size_t)ctx->m);
     AP_CK(cudaMemcpy(bad.data(), ctx->bad, sizeof(int) * ctx->m, cudaMemcpyDeviceToHost));
@@ -351,6 +360,7 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         dfree(ctx, ctx->spart);
         dfree(ctx, ctx->sticket);
         ctx->Cp = 0;
+        ctx->r_tracked_c = 0;
         const size_t nc = (size_t)(ctx->n * Cp);
         AP_TRY(dalloc_t(ctx, &ctx->R, nc));
         AP_TRY(dalloc_t(ctx, &ctx->W, nc));
@@ -384,7 +394,15 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
 ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
     const int Cp = ctx->Cp;
     const bool prof = ctx->o.profile && (size_t)(2 * j + 1) < ctx->ev_up.size();
-    if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j], ctx->st, cudaEventRecordExternal));
+    // timing events: external event nodes while an epoch is being captured
+    // into a graph, plain records when the steps are launched directly
+    unsigned rec_flags = cudaEventRecordDefault;
+    if (prof) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        AP_CK(cudaStreamIsCapturing(ctx->st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+    }
+    if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j], ctx->st, rec_flags));
     SolveParams sp = {};
     sp.Linv = ctx->Linv;
     sp.n = ctx->n;
@@ -409,8 +427,8 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
         ++ctx->launches;
     }
     if (prof) {
-        AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j + 1], ctx->st, cudaEventRecordExternal));
-        AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j], ctx->st, cudaEventRecordExternal));
+        AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j + 1], ctx->st, rec_flags));
+        AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j], ctx->st, rec_flags));
     }
     if (ctx->tc) {
         Shape sh;
@@ -431,13 +449,14 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
         tl.noise = ctx->noise;
         tl.sel = ctx->sel;
         tl.err = ctx->tc_err;
+        tl.wait_cycles = ctx->o.wait_limit_cycles;
         tl.scr = ctx->tc_scr;
         tl.tick = ctx->tc_tick;
         tl.epi = make_epi(ctx, kEpiBlockNorms | (colnorms ? kEpiColNorms : 0), 1, sh);
         const int grid = (int)std::min<int64_t>(ctx->num_sms, sh.ntiles);
         AP_CK(launch_kmv_tc_step(ctx->kernel, tl, ctx->kd, Cp, grid, ctx->st));
         ++ctx->launches;
-        if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j + 1], ctx->st, cudaEventRecordExternal));
+        if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j + 1], ctx->st, rec_flags));
         return AP_OK;
     }
     const Shape sh = step_shape(ctx, Cp, ctx->b);
@@ -458,7 +477,7 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
     kp.epi = make_epi(ctx, kEpiBlockNorms | (colnorms ? kEpiColNorms : 0), 1, sh);
     AP_CK(launch_kmv(ctx->kernel, kp, ctx->D, Cp, ctx->st));
     ++ctx->launches;
-    if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j + 1], ctx->st, cudaEventRecordExternal));
+    if (prof) AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j + 1], ctx->st, rec_flags));
     return AP_OK;
 }
 
@@ -607,12 +626,15 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         ctx->trace_alloc = want_trace;
     }
     const int64_t l0 = ctx->launches;
+    ctx->r_tracked_c = 0;
     AP_TRY(enter(ctx));
     AP_CK(launch_pad_copy(B_dev, ctx->n, c, ctx->Bp, Cp, ctx->st));
     ++ctx->launches;
     AP_CK(cudaMemsetAsync(ctx->step, 0, sizeof(int64_t), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
     AP_CK(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->st));
+    // arrival tickets start at zero (a launch that gave up on a wait leaves them partial)
+    AP_CK(cudaMemsetAsync(ctx->ticket, 0, 4 * sizeof(unsigned), ctx->st));
     if (ctx->tc_tick) AP_CK(cudaMemsetAsync(ctx->tc_tick, 0, sizeof(int) * ctx->num_sms, ctx->st));
     // ||b_c|| for the relative residuals
     AP_TRY(launch_norms(ctx, ctx->Bp, kEpiColNorms));
@@ -700,6 +722,10 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         }
         if (epoch >= ctx->o.max_epochs) break;
         if (ctx->o.max_steps > 0 && steps >= ctx->o.max_steps) break;
+        if (ctx->o.cancel && *ctx->o.cancel) {
+            status = AP_ERR_CANCELLED;
+            break;
+        }
     }
     // A low-precision run that stopped on its epoch cap reports the true
     // residual of the W it returns: one more FP32 recompute (max_steps runs,
@@ -722,6 +748,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
     AP_CK(launch_unpad_copy(ctx->W, ctx->n, Cp, W_dev, c, ctx->st));
     ++ctx->launches;
     AP_TRY(leave(ctx));
+    ctx->r_tracked_c = c;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);
     if (ctx->o.block_trace && ctx->o.trace_cap > 0) {
@@ -759,6 +786,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
 namespace ap {
 
 void ctx_grad_view(const ap_ctx* ctx, GradView* v) {
+    v->device = ctx->device;
     v->Xs = ctx->Xs;
     v->n = ctx->n;
     v->d = ctx->d;
@@ -818,6 +846,7 @@ const char* ap_status_str(ap_status s) {
         case AP_ERR_CUDA: return "AP_ERR_CUDA";
         case AP_ERR_UNSUPPORTED: return "AP_ERR_UNSUPPORTED";
         case AP_ERR_SCRATCH_LIMIT: return "AP_ERR_SCRATCH_LIMIT";
+        case AP_ERR_CANCELLED: return "AP_ERR_CANCELLED";
     }
     return "AP_ERR_UNKNOWN";
 }
@@ -851,9 +880,13 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
     ctx->cpb = tc_chunks_per_block(ctx->b);
     ctx->tps128 = (ctx->b + 127) / 128;
     {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        int sms = 0;
+        if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return AP_ERR_CUDA;
+        }
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess && sms > 0)
             ctx->num_sms = sms;
         cudaGetLastError();
     }
@@ -916,6 +949,7 @@ ap_status ap_create(ap_ctx** out, const float* X_dev, int64_t n, int32_t d, cons
 
 ap_status ap_set_hyper(ap_ctx* ctx, const ap_hyper* h) {
     if (!ctx) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     AP_TRY(check_hyper(h, ctx->d));
     if (h->kernel != ctx->kernel) return AP_ERR_INVALID_ARG;
     copy_hyper(ctx, h);
@@ -925,6 +959,7 @@ ap_status ap_set_hyper(ap_ctx* ctx, const ap_hyper* h) {
 
 ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_dev, float* W_dev, ap_info* info) {
     if (!ctx || !B_dev || !W_dev || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     ap_status s = solve_impl(ctx, B_dev, c, W0_dev, W_dev, info);
     if (info && s != AP_OK) info->bad_block = -1;
     return s;
@@ -932,8 +967,10 @@ ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_d
 
 ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W_dev, float* R_dev) {
     if (!ctx || !B_dev || !W_dev || !R_dev || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     const int Cp = pad_c(c);
     AP_TRY(ensure_solve(ctx, Cp));
+    ctx->r_tracked_c = 0;
     AP_TRY(enter(ctx));
     AP_CK(launch_pad_copy(B_dev, ctx->n, c, ctx->Bp, Cp, ctx->st));
     AP_CK(launch_pad_copy(W_dev, ctx->n, c, ctx->Tmp, Cp, ctx->st));
@@ -946,6 +983,7 @@ ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W
 
 ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, int64_t M, float* mean_dev) {
     if (!ctx || !w_dev || !Xs_dev || !mean_dev || M < 1) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     if (M > ctx->Xt_alloc) {
         dfree(ctx, ctx->Xt);
         ctx->Xt_alloc = 0;
@@ -953,6 +991,7 @@ ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, 
         ctx->Xt_alloc = M;
     }
     AP_TRY(enter(ctx));
+    AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
     AP_TRY(prep_inputs(ctx, Xs_dev, M, ctx->Xt, nullptr));
     const int64_t rows = kmv_rows_per_cta(ctx->D, 1);
     Shape sh;
@@ -979,7 +1018,10 @@ ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, 
     kp.epi.seg = M;
     AP_CK(launch_kmv(ctx->kernel, kp, ctx->D, 1, ctx->st));
     ++ctx->launches;
-    return leave(ctx);
+    int nanx = 0;
+    AP_CK(cudaMemcpyAsync(&nanx, ctx->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    AP_TRY(leave(ctx));
+    return nanx ? AP_ERR_NAN : AP_OK;
 }
 
 static ap_status grad_quadforms_impl(ap_ctx* ctx, const float* U, const float* V, int Cp, const double* alpha,
@@ -1021,6 +1063,7 @@ static ap_status grad_quadforms_impl(ap_ctx* ctx, const float* U, const float* V
 ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c, const double* alpha_host,
                             double* out_host) {
     if (!ctx || !U_dev || !V_dev || !alpha_host || !out_host || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     const int Cp = pad_c(c);
     AP_TRY(ensure_solve(ctx, Cp));
     AP_TRY(enter(ctx));
@@ -1034,6 +1077,7 @@ ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev,
 ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const float* Z_dev, float* grad_host,
                       ap_info* info) {
     if (!ctx || !y_dev || !grad_host || n_probes < 0 || n_probes + 1 > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
     const int l = n_probes, c = l + 1;
     float* Bfull = nullptr;
     float* Wfull = nullptr;
@@ -1082,6 +1126,20 @@ ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const f
 
 int64_t ap_launch_count(const ap_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int32_t ap_last_cuda_error(const ap_ctx* ctx) { return ctx ? (int32_t)ctx->last_cuda : 0; }
+
+size_t ap_device_bytes(const ap_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+ap_status ap_tracked_residual(ap_ctx* ctx, int32_t c, float* R_dev) {
+    if (!ctx || !R_dev || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
+    if (ctx->r_tracked_c != c || !ctx->R) return AP_ERR_INVALID_ARG;
+    AP_DEVICE_GUARD(ctx);
+    AP_TRY(enter(ctx));
+    AP_CK(launch_unpad_copy(ctx->R, ctx->n, ctx->Cp, R_dev, c, ctx->st));
+    ++ctx->launches;
+    return leave(ctx);
+}
+
 ap_status ap_phi_fp64_eval(int32_t kernel, const double* r2_host, int64_t count, double* phi_host) {
     if (kernel < AP_RBF || kernel > AP_MATERN52 || count < 0) return AP_ERR_INVALID_ARG;
     if (count == 0) return AP_OK;
@@ -1108,6 +1166,7 @@ ap_status ap_phi_fp64_eval(int32_t kernel, const double* r2_host, int64_t count,
 
 void ap_destroy(ap_ctx* ctx) {
     if (!ctx) return;
+    DeviceGuard dg(ctx->device);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     free_all(ctx);
     delete ctx;

@@ -149,7 +149,7 @@ cudaError_t launch_block_solve(const SolveParams& p, cudaStream_t st, int64_t* l
 // Xs = fl(X * sc) with sc = sc_hi + sc_lo per dimension; Xs_lo (may be null)
 // gets the remainder X * sc - Xs to FP32 precision.
 cudaError_t launch_prep_inputs(const float* X, int64_t n, int d, int D, const float* sc_hi, const float* sc_lo,
-                               float* Xs, float* Xs_lo, cudaStream_t st);
+                               float* Xs, float* Xs_lo, int* bad, cudaStream_t st);
 cudaError_t launch_pad_copy(const float* src, int64_t n, int c, float* dst, int C, cudaStream_t st);
 cudaError_t launch_unpad_copy(const float* src, int64_t n, int C, float* dst, int c, cudaStream_t st);
 
@@ -209,6 +209,7 @@ struct TcLaunch {
     float s, noise;
     const int* sel;
     int* err;
+    long long wait_cycles;  // bound of the kernel's waits (<= 0: the default, about 2 s)
     float* scr;  // grid x 2 x 128 x C floats (tc_share_bytes)
     int* tick;   // grid ints, zero
     EpiParams epi;
@@ -217,8 +218,27 @@ struct TcLaunch {
 size_t tc_share_bytes(int grid, int C);
 cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int grid, cudaStream_t st);
 
+// Makes the context's device current for one call and restores the caller's.
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+        if (ok_ && prev_ != dev) ok_ = cudaSetDevice(dev) == cudaSuccess, switched_ = ok_;
+        if (!ok_) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (switched_) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+
+   private:
+    int prev_ = 0;
+    bool ok_ = false, switched_ = false;
+};
+
 // Read-only view of what the gradient kernel needs from a context.
 struct GradView {
+    int device;           // the context's device
     const float* Xs;
     int64_t n;
     int d, D, kernel;

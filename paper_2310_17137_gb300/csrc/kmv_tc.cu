@@ -153,6 +153,7 @@ struct TcParams {
     float s, noise;
     const int* sel;
     int* err;              // timeout flag
+    long long wait_cycles; // bound of every mbarrier wait, in SM clock cycles
     float* scr;            // gridDim.x x 2 x 128 x C: partial accumulators of the tiles two CTAs share
     int* tick;             // gridDim.x arrival counters of those tiles (0 between launches)
     EpiParams epi;         // tiles of 128 rows aligned to blocks (tiles_per_seg = ceil(b / 128))
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             auto issue_xa = [&](int64_t sg, int64_t tile) -> bool {
                 const int xb = (int)(sg & 1);
                 const int64_t u = sg >> 1;
-                if (u >= 1 && !mbar_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1), &s_abort, p.err)) return false;
+                if (u >= 1 && !mbar_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1), &s_abort, p.err, p.wait_cycles)) return false;
                 mbar_expect_tx(&bar_xa_full[xb], kXaBytes);
                 bulk_g2s(s_xa + (size_t)xb * kXaBytes, p.XA + (size_t)tile * kXaBytes, kXaBytes, &bar_xa_full[xb]);
                 return true;
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 if ((i == 0 || q == 0) && tile < last_tile) ok = issue_xa(sg + 1, tile + 1);
                 const int s = (int)(i % kStages);
                 const int64_t u = i / kStages;
-                if (ok && u >= 1) ok = mbar_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1), &s_abort, p.err);
+                if (ok && u >= 1) ok = mbar_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1), &s_abort, p.err, p.wait_cycles);
                 if (!ok) break;
                 uint8_t* dst = s_stage + (size_t)s * kStageBytes;
                 mbar_expect_tx(&bar_stage_full[s], kStageBytes);
@@ -280,15 +281,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 if (g == 0 || q == 0) {
                     ++sg;
                     xb = (int)(sg & 1);
-                    ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((sg >> 1) & 1), &s_abort, p.err);
+                    ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((sg >> 1) & 1), &s_abort, p.err, p.wait_cycles);
                     xa = smem_u32(s_xa + (size_t)xb * kXaBytes);
                     if (!ok) break;
                 }
                 const int s = (int)(g % kStages);
                 const int buf = (int)(g % kBufs);
                 const int64_t use = g / kBufs;
-                ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err);
-                if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err);
+                ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err, p.wait_cycles);
+                if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err, p.wait_cycles);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t xbs = smem_u32(s_stage + (size_t)s * kStageBytes);
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 const bool first = g == 0 || q == 0;
                 const int buf = (int)(g % kBufs);
                 const int s = (int)(g % kStages);
-                if (first && ++sg >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((sg - 1) & 1), &s_abort, p.err);
+                if (first && ++sg >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((sg - 1) & 1), &s_abort, p.err, p.wait_cycles);
                 if (!ok) break;
                 // Delta^T of the stage: C rows of Delta_hi, then C rows of Delta_lo
                 // (consecutive 8-row groups), so one N = 2C product gives hi*hi
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
 #pragma unroll
                 for (int ks = 0; ks < KSTEPS_C; ++ks) {
                     if (ks % kUnits == 0) {
-                        ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err);
+                        ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err, p.wait_cycles);
                         if (!ok) break;
                         tc_fence_after();
                     }
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         // part 0 + part 1, in that order whichever arrives last.  Every path passes
         // the same named barriers so that a failed wait cannot strand the others.
         auto epilogue = [&](int sg, int64_t tile, bool whole, int part) {
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(sg & 1), &s_abort, p.err));
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(sg & 1), &s_abort, p.err, p.wait_cycles));
             if (ok) tc_fence_after();
             const int64_t segi = tile / e.tiles_per_seg;
             const int64_t seg_lo = segi * e.seg;
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             uint32_t ta[16], tb[16];
             if (ok)
                 ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[c % kBufs], (uint32_t)((c / kBufs) & 1),
-                                                      &s_abort, p.err));
+                                                      &s_abort, p.err, p.wait_cycles));
             if (ok) {
                 tc_fence_after();
                 tmem_ld16(u_addr(c, 0), ta);
@@ -725,6 +726,7 @@ cudaError_t launch_kmv_tc_step(int kernel, const TcLaunch& l, int kd, int C, int
     p.noise = l.noise;
     p.sel = l.sel;
     p.err = l.err;
+    p.wait_cycles = l.wait_cycles > 0 ? l.wait_cycles : tc::kWaitCycles;
     p.scr = l.scr;
     p.tick = l.tick;
     p.epi = l.epi;

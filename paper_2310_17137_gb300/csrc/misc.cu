@@ -31,9 +31,10 @@ struct ScaleVec {
 
 // Xs[i, k] = fl(X[i, k] * sc_k) for k < d, 0 for the padding k in [d, D);
 // sc_k = hi_k + lo_k, and Xs_lo gets X * sc_k - Xs (TwoProd remainder plus
-// the lo part of the scale) when requested.
+// the lo part of the scale) when requested.  A NaN or Inf input sets *bad.
 __global__ void prep_inputs_kernel(const float* __restrict__ X, int64_t n, int d, int D, const ScaleVec sh,
-                                   const ScaleVec sl, float* __restrict__ Xs, float* __restrict__ Xs_lo) {
+                                   const ScaleVec sl, float* __restrict__ Xs, float* __restrict__ Xs_lo,
+                                   int* __restrict__ bad) {
     const int64_t total = n * D;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -42,6 +43,7 @@ __global__ void prep_inputs_kernel(const float* __restrict__ X, int64_t n, int d
         float hi = 0.0f, lo = 0.0f;
         if (k < d) {
             const float x = X[i * d + k];
+            if (!isfinite(x) && bad) *bad = 1;
             hi = x * sh.v[k];
             lo = fmaf(x, sh.v[k], -hi) + x * sl.v[k];
         }
@@ -80,13 +82,13 @@ unsigned grid_for(int64_t total) {
 }  // namespace
 
 cudaError_t launch_prep_inputs(const float* X, int64_t n, int d, int D, const float* sc_hi, const float* sc_lo,
-                               float* Xs, float* Xs_lo, cudaStream_t st) {
+                               float* Xs, float* Xs_lo, int* bad, cudaStream_t st) {
     ScaleVec sh = {}, sl = {};
     for (int k = 0; k < d && k < AP_MAX_DIM; ++k) {
         sh.v[k] = sc_hi[k];
         sl.v[k] = sc_lo ? sc_lo[k] : 0.0f;
     }
-    prep_inputs_kernel<<<grid_for(n * D), 256, 0, st>>>(X, n, d, D, sh, sl, Xs, Xs_lo);
+    prep_inputs_kernel<<<grid_for(n * D), 256, 0, st>>>(X, n, d, D, sh, sl, Xs, Xs_lo, bad);
     return cudaGetLastError();
 }
 

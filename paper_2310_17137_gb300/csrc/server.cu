@@ -43,6 +43,7 @@ struct Job {
     int epochs = 0;
     double rel_res = 0.0;
     bool done = false;
+    volatile int32_t cancel = 0;  // read by the solve between epochs
 };
 
 // Device bytes a request needs: inputs and outputs, the scaled inputs, the FP32
@@ -135,6 +136,7 @@ ap_status run_job(ap_server* srv, Job* j, cudaStream_t st) {
     o.precision = r.precision;
     o.refine_every = r.refine_every > 0 ? r.refine_every : 4;
     o.stream = st;
+    o.cancel = &j->cancel;
     const size_t inputs = sizeof(float) * (size_t)(r.n * r.d + 3 * r.n + r.M * r.d + r.M);
     o.hbm_budget = j->reserve > inputs ? j->reserve - inputs : 0;
     ap_hyper h = r.hyper;
@@ -147,7 +149,7 @@ ap_status run_job(ap_server* srv, Job* j, cudaStream_t st) {
     }
     ap_info info;
     memset(&info, 0, sizeof(info));
-    s = ap_solve(ctx, B, 1, nullptr, W, &info);
+    s = j->cancel ? AP_ERR_CANCELLED : ap_solve(ctx, B, 1, nullptr, W, &info);
     j->epochs = info.epochs;
     j->rel_res = info.rel_res_true[0];
     if (s == AP_OK || s == AP_ERR_NOT_CONVERGED) {
@@ -281,6 +283,31 @@ ap_status ap_server_poll(ap_server* srv, int64_t id, ap_request_result* res) {
     res->queue_s = (j->t_start > 0 ? j->t_start : now_s()) - j->t_submit;
     res->latency_s = j->done ? j->t_done - j->t_submit : 0.0;
     res->reserved_bytes = j->reserve;
+    res->started = j->t_start > 0 ? 1 : 0;
+    return AP_OK;
+}
+
+ap_status ap_server_cancel(ap_server* srv, int64_t id) {
+    if (!srv) return AP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->jobs.find(id);
+        if (it == srv->jobs.end()) return AP_ERR_INVALID_ARG;
+        Job* j = it->second.get();
+        if (j->done) return AP_OK;
+        j->cancel = 1;
+        for (auto p = srv->pending.begin(); p != srv->pending.end(); ++p) {
+            if (*p == j) {
+                // never admitted: nothing reserved, nothing on the device
+                srv->pending.erase(p);
+                j->status = AP_ERR_CANCELLED;
+                j->t_done = now_s();
+                j->done = true;
+                break;
+            }
+        }
+    }
+    srv->cv_done.notify_all();
     return AP_OK;
 }
 

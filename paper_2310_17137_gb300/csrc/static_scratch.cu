@@ -3,14 +3,13 @@
 //
 // Why it exists: ap_grad_quadforms may grow context work buffers with
 // cudaMalloc on its first use with a given size.  Some callers cannot let that
-// happen inside their steady-state loop: code that runs while a CUDA stream is
-// being captured into a graph (an allocation there is not recorded in the graph
-// and cudaMalloc/cudaFree synchronise the device), latency-bound serving loops
-// (the same implicit synchronisation stalls every stream), and hosts whose
-// memory pool already owns all free HBM (a cudaMalloc would fail).  They build
-// the context once at set-up and then call this entry point, which uses only
-// the buffers the caller passes and one fixed scratch array compiled into the
-// library.
+// happen once their steady state has begun: latency-bound serving loops
+// (cudaMalloc and cudaFree synchronise the whole device, stalling every other
+// stream) and processes whose own memory pool already holds all free HBM (a
+// cudaMalloc would fail).  They build the context once at set-up and then call
+// this entry point, which uses only the buffers the caller passes and one
+// fixed scratch array compiled into the library.  The call still copies its
+// sums to the host and synchronises the context's stream before returning.
 #include <mutex>
 
 #include "ap_internal.cuh"
@@ -33,16 +32,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device.
-cudaError_t scratch_on_current_device(double** out) {
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
+// Device address of g_scratch on device `dev`, which must be current; looked
+// up once per device (a host-side name of a __device__ array is not a device
+// address).
+cudaError_t scratch_on_device(int dev, double** out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ptr[dev]) {
         void* p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_scratch);
+        const cudaError_t err = cudaGetSymbolAddress(&p, g_scratch);
         if (err != cudaSuccess) return err;
         g_ptr[dev] = static_cast<double*>(p);
     }
@@ -65,8 +63,10 @@ extern "C" ap_status ap_grad_quadforms_static(ap_ctx* ctx, const float* U_dev, c
     const int64_t rows = grad_rows_per_cta(v.D, c);
     const int64_t ntiles = (v.n + rows - 1) / rows;
     if ((size_t)(kPartOff + ntiles * NA) > kScratchDoubles) return AP_ERR_SCRATCH_LIMIT;
+    DeviceGuard dg(v.device);  // the context's device is current for the look-up and the launch
+    if (!dg.ok()) return AP_ERR_CUDA;
     double* scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) {
+    if (scratch_on_device(v.device, &scratch) != cudaSuccess) {
         cudaGetLastError();
         return AP_ERR_CUDA;
     }

@@ -33,28 +33,32 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 // the phase completes (or the hint expires) instead of spinning on the issue
 // slots the transform warps need.
 constexpr uint32_t kSuspendHintNs = 1000000;
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, uint32_t hint_ns = kSuspendHintNs) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase.  Gives up when the deadline passes or when
-// another thread of the CTA already gave up (abort flag), and reports it.
+// Bounded wait on an mbarrier phase.  Gives up when `limit` SM clock cycles
+// have passed or when another thread of the CTA already gave up (abort flag),
+// and reports it.
+// A bound shorter than the default also drops the suspend hint, so that the
+// bound is what ends the wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
+                                          int* err_flag, long long limit = kWaitCycles) {
+    const uint32_t hint = limit >= kWaitCycles ? kSuspendHintNs : 0u;
+    if (mbar_try_wait(bar, parity, hint)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity, hint)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicExch(err_flag, 1);
             return false;

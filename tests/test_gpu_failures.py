@@ -1,0 +1,108 @@
+"""Failure paths of the solver, made on the host or by a short wait bound, never
+by faulting the GPU: NaN / Inf inputs give AP_ERR_NAN; a device wait of the
+tensor-core update that runs out ends the kernel and gives AP_ERR_TIMEOUT,
+after which the device is still usable; a cancel flag stops a solve at the end
+of an epoch with AP_ERR_CANCELLED and a usable iterate."""
+import ctypes
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2310_17137_gb300 as ap
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+
+
+def _hyper(p):
+    return ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+
+
+@pytest.mark.parametrize("prec", [ap.AP_FP32, ap.AP_BF16_REFINE], ids=["fp32", "bf16"])
+def test_nan_in_rhs_is_reported(prec):
+    p = wl.random_problem(1500, 4, 256, 4, wl.MATERN52, 0.05, 41)
+    B = p.B.copy()
+    B[777, 2] = np.nan
+    ctx = ap.ap_create(_t(p.X), _hyper(p), ap.ap_opts_default(block=p.block, precision=prec, max_epochs=5))
+    with pytest.raises(ap.ApError) as e:
+        ap.ap_solve(ctx, _t(B))
+    assert e.value.status == ap.AP_ERR_NAN
+    # the context still solves a clean right-hand side
+    st, W, info, _ = ap.ap_solve(ctx, _t(p.B))
+    assert st in (ap.AP_OK, ap.AP_ERR_NOT_CONVERGED) and np.all(np.isfinite(W.cpu().numpy()))
+    ap.ap_destroy(ctx)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nan_in_inputs_is_reported(bad):
+    p = wl.random_problem(900, 3, 256, 1, wl.RBF, 0.05, 42)
+    X = p.X.copy()
+    X[123, 1] = bad
+    with pytest.raises(ap.ApError) as e:
+        ap.ap_create(_t(X), _hyper(p), ap.ap_opts_default(block=p.block))
+    assert e.value.status == ap.AP_ERR_NAN
+    ctx = ap.ap_create(_t(p.X), _hyper(p), ap.ap_opts_default(block=p.block))
+    Xt = wl.test_points(p, m=64)
+    Xt[5, 0] = bad
+    with pytest.raises(ap.ApError) as e:
+        ap.ap_predict_mean(ctx, _t(np.ones(p.n)), _t(Xt))
+    assert e.value.status == ap.AP_ERR_NAN
+    ap.ap_destroy(ctx)
+
+
+def test_wait_that_runs_out_gives_timeout_and_the_device_stays_usable():
+    # a one-cycle bound (and no suspend hint) on every mbarrier wait of the
+    # tensor-core update: the first wait that is not already complete gives up,
+    # the kernel lets its copies and MMAs land, frees its tensor memory and returns
+    p = wl.random_problem(5000, 3, 512, 16, wl.MATERN52, 0.05, 43)
+    ctx = ap.ap_create(_t(p.X), _hyper(p), ap.ap_opts_default(block=p.block, precision=ap.AP_BF16_REFINE,
+                                                              wait_limit_cycles=1, max_epochs=2))
+    with pytest.raises(ap.ApError) as e:
+        ap.ap_solve(ctx, _t(p.B))
+    assert e.value.status == ap.AP_ERR_TIMEOUT
+    ap.ap_destroy(ctx)
+    torch.cuda.synchronize()
+    # the same problem with the default bound, checked against the oracle's replay
+    k = 5
+    ctx = ap.ap_create(_t(p.X), _hyper(p), ap.ap_opts_default(block=p.block, precision=ap.AP_BF16_REFINE, tol=1e-30,
+                                                              min_epochs=0, max_steps=k, refine_every=0), trace_cap=k)
+    st, W, info, trace = ap.ap_solve(ctx, _t(p.B))
+    assert st == ap.AP_ERR_NOT_CONVERGED and info["steps"] == k
+    r = oracle.ap_solve(oracle.Hyper.of(p), p.X.astype(np.float64), p.B.astype(np.float64), p.block,
+                        select=oracle.SEL_FORCED, forced=trace, max_steps=k)
+    assert np.abs(W.cpu().numpy() - r.W).max() <= 1e-2 * np.abs(r.W).max()
+    ap.ap_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [ap.AP_FP32, ap.AP_BF16_REFINE], ids=["fp32", "bf16"])
+def test_cancel_flag_stops_a_solve_between_epochs(prec):
+    p = wl.random_problem(20000, 3, 1024, 4, wl.MATERN52, 0.01, 44)
+    flag = ctypes.c_int32(0)
+    opts = ap.ap_opts_default(block=p.block, precision=prec, tol=1e-30, min_epochs=0, max_epochs=1_000_000,
+                              refine_every=10)
+    opts.cancel = ctypes.addressof(flag)
+    ctx = ap.ap_create(_t(p.X), _hyper(p), opts)
+    out = {}
+
+    def run():
+        try:
+            out["res"] = ap.ap_solve(ctx, _t(p.B))
+        except ap.ApError as err:
+            out["err"] = err
+
+    th = threading.Thread(target=run)
+    th.start()
+    time.sleep(1.0)
+    flag.value = 1
+    th.join(timeout=60)
+    assert not th.is_alive()
+    assert "err" in out and out["err"].status == ap.AP_ERR_CANCELLED
+    ap.ap_destroy(ctx)
