@@ -2,16 +2,24 @@
 """Benchmark of the alternating-projection hot path on one or more GPUs.
 
 One step = one whole pass of the hot path on one synthetic problem: scale the
-inputs and build the FP64 block-Cholesky cache (ap_create), then run Alg. 1 to
-the tolerance with the fused residual update, Gauss-Southwell selection and the
-FP32 recompute that certifies the stopping rule (ap_solve).
+inputs and build the FP64 block-Cholesky cache (ap_create), then run Alg. 1 with
+the fused residual update, Gauss-Southwell selection and the FP32 recompute
+that refines and certifies (ap_solve).
 
-Workload (default): n = 262,144, d = 3, X ~ N(0, I), Matern-5/2 ARD with
-lengthscales log-uniform in [0.3, 3], noise 1e-2, blocks of 4096, B = [y, 15
-Rademacher probes], every column solved to ||r|| / ||b|| <= 1e-3.
+Workload of the timed steps (default): n = 262,144, d = 3, X ~ N(0, I),
+Matern-5/2 ARD with lengthscales log-uniform in [0.3, 3], noise 1e-2, blocks of
+4096, B = [y, 15 Rademacher probes], every column to ||r|| / ||b|| <= 1e-3,
+capped at 30 epochs (the tolerance is out of AP's reach on this workload).
 
 value = kernel-matrix entries evaluated per second over the whole step (the
 n*b entries of the cache plus n*b per AP step plus n^2 per FP32 recompute).
+
+Also in the line: the other form on the same workload; e2e = the same step
+through the host-buffer entry point ap_solve_host with its copies timed;
+time-to-tolerance of the FP32 form on n = 4096 (RBF, tol 1e-6) and of both forms
+on n = 2,097,152 (d = 11, RBF ARD, noise 1e-3, blocks of 8192, y column to 1e-2);
+the MLL gradient on n = 131,072 (Matern-3/2, 31 probes); a serving replay; the
+FP64 oracle on the host cores (cpu_baseline).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload and prints the same kind of line.
@@ -39,6 +47,7 @@ import numpy as np  # noqa: E402
 import workloads as wl  # noqa: E402
 
 METRIC = "AP time-to-tol & kernel-entries/s, BF16+refine vs FP32; serve p50/p99"
+T_START = time.perf_counter()
 # forms of the residual update: FP32 SIMT, tensor-core BF16 hi/lo
 FORMS = {"fp32": lambda ap: ap.AP_FP32, "bf16": lambda ap: ap.AP_BF16_REFINE}
 DTYPES = {"fp32": "f32", "bf16": "bf16"}
@@ -240,66 +249,86 @@ def run_ours(args, rank: int, world: int):
             c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             c0.record(stream)
             cinfos = []
-            for _ in range(args.steps):
+            csteps = min(args.steps, args.compare_steps)
+            for _ in range(csteps):
                 _, ci, _ = one_step(other)
                 cinfos.append(ci)
             c1.record(stream)
             torch.cuda.synchronize()
-            cms = c0.elapsed_time(c1) / args.steps
+            cms = c0.elapsed_time(c1) / csteps
             cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / args.steps
             compare[name] = {"ms_per_step": cms, "kernel_entries_per_s": cent / (cms * 1e-3),
                              "update_kernel_ms": cinfos[-1]["t_update_s"] / max(1, cinfos[-1]["n_update"]) * 1e3,
                              "solve_s": statistics.median(i["t_solve_s"] for i in cinfos),
                              "rel_res_y": cinfos[-1]["rel_res_true"][0],
                              "rel_res_max": max(cinfos[-1]["rel_res_true"]),
-                             "epochs": cinfos[-1]["epochs"], "refinements": cinfos[-1]["refinements"]}
+                             "epochs": cinfos[-1]["epochs"], "refinements": cinfos[-1]["refinements"],
+                             "steps_timed": csteps}
 
     # end to end through the public API with host buffers (pinned), copies timed
-    e2e_value = None
+    e2e_value, e2e_steps = None, 0
     if not args.no_e2e:
-        e2e_value = end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist)
+        e2e_value, e2e_steps = end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist)
     ttt = None
     if rank == 0 and not args.no_ttt:
         ttt = time_to_tol_small(ap, torch, dev, stream)
     mll = None
     if rank == 0 and not args.no_mll:
         mll = mll_grad_timing(ap, torch, dev, stream)
+    # the long legs run only while the whole run stays inside its time budget
+    # (estimates from measured runs on this workload: 13.5 min and 3 min)
+    def budget_left() -> float:
+        return args.time_budget_s - (time.perf_counter() - T_START)
+
+    ttt_large = None
+    if rank == 0 and not args.no_ttt_large:
+        ttt_large = (time_to_tol_large(ap, torch, dev, stream, args) if budget_left() > 900
+                     else {"skipped": f"time budget ({args.time_budget_s:.0f} s) nearly used"})
+    serve = None
+    if rank == 0 and not args.no_serve_replay:
+        serve = (serving_replay(ap, args, args.serve_replay_requests, args.serve_max_epochs) if budget_left() > 240
+                 else {"skipped": f"time budget ({args.time_budget_s:.0f} s) nearly used"})
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt)
+    line = result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt,
+                       e2e_steps)
     line["other_forms"] = compare
     line["mll_grad"] = mll
+    line["time_to_tol_large"] = ttt_large
+    line["serving"] = serve
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, infos[-1]["epochs"], args)
+        if not args.no_ttt:
+            line["cpu_baseline"]["time_to_tol_small"] = oracle_time_to_tol_small()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
 def end_to_end(ap, torch, p, hyper, opts, dev, stream, args, dist):
+    """The same step through the one-shot host-buffer entry point ap_solve_host:
+    X and B copied in from page-locked host memory, the cache built, Alg. 1 run,
+    W copied out, every step inside the timed region."""
     Xh = torch.from_numpy(p.X).pin_memory()
     Bh = torch.from_numpy(p.B).pin_memory()
     Wh = torch.empty(p.B.shape, dtype=torch.float32).pin_memory()
+    Xn, Bn, Wn = Xh.numpy(), Bh.numpy(), Wh.numpy()
+    steps = min(args.steps, args.e2e_steps)
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     e2e_entries = 0.0
     cache_entries = float(p.n) * float(p.block)
-    for _ in range(args.steps):
-        Xd = Xh.to(dev, non_blocking=True)
-        Bd = Bh.to(dev, non_blocking=True)
-        ctx = ap.ap_create(Xd, hyper, opts())
-        st, Wd, info, _ = ap.ap_solve(ctx, Bd)
-        Wh.copy_(Wd, non_blocking=True)
-        ap.ap_destroy(ctx)
+    for _ in range(steps):
+        _, _, info = ap.ap_solve_host(Xn, Bn, hyper, opts(), W=Wn)
         e2e_entries += cache_entries + info["kernel_entries"]
     e3.record(stream)
     torch.cuda.synchronize()
     e2e_ms, e2e_entries = aggregate(e2.elapsed_time(e3), e2e_entries, dist, dev)
-    return e2e_entries / (e2e_ms * 1e-3)
+    return e2e_entries / (e2e_ms * 1e-3), steps
 
 
 def time_to_tol_small(ap, torch, dev, stream) -> dict:
@@ -325,6 +354,77 @@ def time_to_tol_small(ap, torch, dev, stream) -> dict:
     return {"workload": "small_rbf n=4096 d=8 b=512 c=1 tol=1e-6 (FP32 form, compensated certification)",
             "time_to_tol_s": statistics.median(times), "epochs": i["epochs"], "refinements": i["refinements"],
             "rel_res_true": i["rel_res_true"][0], "status": ap.ap_status_str(st)}
+
+
+def time_to_tol_large(ap, torch, dev, stream, args) -> dict:
+    """Time-to-tolerance of both forms on n = 2,097,152, d = 11, X ~ U[-1,1]^11,
+    RBF ARD (lengthscales log-uniform in [0.2, 2]), noise 1e-3, blocks of 8192,
+    B = [y, 15 Rademacher probes]: each form runs Alg. 1 until the y column's
+    relative residual, recomputed over all n^2 entries in FP32 (the
+    certification the solver applies whenever its rule holds), is at most
+    1e-2.  One run per form, the Cholesky cache included; kernel blocks are
+    never stored."""
+    p = wl.rbf_ard_large()
+    X = torch.from_numpy(p.X).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    hyper = ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean)
+    out = {"workload": f"{p.name}: RBF ARD, n={p.n}, d={p.d}, b={p.block}, c={p.c} (y + {p.c - 1} probes), "
+                       f"noise={p.noise:g}, y column to ||r||/||y|| <= {p.tol:g} (FP32 recompute)"}
+    for name in ("bf16", "fp32"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = ap.ap_create(X, hyper, ap.ap_opts_default(block=p.block, tol=p.tol, stop=ap.AP_STOP_Y_REL, min_epochs=1,
+                                                        max_epochs=args.ttt_large_max_epochs,
+                                                        precision=FORMS[name](ap), refine_every=args.refine_every,
+                                                        residual_mode=ap.AP_RESID_FP32, profile=1,
+                                                        stream=stream.cuda_stream))
+        st, _, info, _ = ap.ap_solve(ctx, B)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        ap.ap_destroy(ctx)
+        out[name] = {"time_to_tol_s": t, "status": ap.ap_status_str(st), "epochs": info["epochs"],
+                     "refinements": info["refinements"], "fp32_epochs": info["fp32_epochs"],
+                     "cache_s": info["t_cache_s"], "solve_s": info["t_solve_s"], "refine_s": info["t_refine_s"],
+                     "rel_res_y": info["rel_res_true"][0], "rel_res_max": max(info["rel_res_true"][:p.c]),
+                     "update_kernel_ms": info["t_update_s"] / max(1, info["n_update"]) * 1e3}
+    out["speedup_bf16_vs_fp32"] = out["fp32"]["time_to_tol_s"] / out["bf16"]["time_to_tol_s"]
+    del X, B
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_replay(ap, args, n_requests: int, max_epochs: int) -> dict:
+    """Replay of the serving workload (Poisson arrivals at `rate`/s, n
+    log-uniform in [2^10, 2^18], d in {3..20}, RBF or Matern-5/2, tolerance
+    1e-2 or 1e-4, half of the requests in the tensor-core form, solve +
+    posterior mean on 1024 test points, 120 GB budget): latency percentiles,
+    solves/s, and every request that did not reach its tolerance."""
+    trace = wl.serving_trace(n_requests=n_requests, rate=args.serve_rate)
+    data = [wl.request_data(r, m_test=1024) for r in trace]
+    srv = ap.ApServer(hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    t0 = time.perf_counter()
+    ids = []
+    for r, (X, y, Xt) in zip(trace, data):
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        h = ap.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise, 0.0)
+        prec = ap.AP_BF16_REFINE if r.low_precision else ap.AP_FP32
+        ids.append(srv.submit(X, y, Xt, h, block=min(r.n, 4096), tol=r.tol, stop=ap.AP_STOP_Y_REL, min_epochs=1,
+                              max_epochs=max_epochs, precision=prec))
+    res = [srv.wait(i, timeout_s=3600.0) for i in ids]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([x["latency_s"] for x in res])
+    missed = [{"n": r.n, "d": r.d, "tol": r.tol, "form": "bf16" if r.low_precision else "fp32",
+               "rel_res": x["rel_res"], "epochs": x["epochs"], "status": ap.ap_status_str(x["status"])}
+              for r, x in zip(trace, res) if x["status"] != ap.AP_OK]
+    return {"requests": len(res), "solves_per_s": len(res) / wall, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s": float(np.mean([x["queue_s"] for x in res])),
+            "wall_s": wall, "converged": len(res) - len(missed), "max_epochs": max_epochs, "not_converged": missed,
+            "config": f"{len(res)} requests, Poisson {args.serve_rate}/s, n logU[2^10, 2^18], d U{{3..20}}, RBF or "
+                      f"Matern-5/2, tol {{1e-2, 1e-4}} on the y column, solve + mean on 1024 test points, half in "
+                      f"the tensor-core form, {args.serve_budget_gb:g} GB budget, {args.serve_slots} slots"}
 
 
 def mll_grad_timing(ap, torch, dev, stream) -> dict:
@@ -360,7 +460,8 @@ def mll_grad_timing(ap, torch, dev, stream) -> dict:
             "grad_norm": float(np.linalg.norm(grads[-1].astype(np.float64)))}
 
 
-def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt) -> dict:
+def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, clocks, e2e_value, ttt,
+                e2e_steps=0) -> dict:
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     last = infos[-1]
@@ -386,6 +487,7 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "config": describe(p, args),
         "epochs": [i["epochs"] for i in infos],
         "refinements": [i["refinements"] for i in infos],
+        "fp32_epochs": [i["fp32_epochs"] for i in infos],
         "refine_s": statistics.median(i["t_refine_s"] for i in infos),
         "status": [ap.ap_status_str(s) for s in statuses],
         "rel_res_max": max(max(i["rel_res_true"]) for i in infos),
@@ -398,7 +500,8 @@ def result_line(ap, p, args, world, ms_max, value, infos, statuses, launches, cl
         "roofline": roof,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": "kernel-entries/s",
-            "h2d_bytes_per_step": int(p.X.nbytes + p.B.nbytes), "d2h_bytes_per_step": int(p.B.nbytes)},
+            "h2d_bytes_per_step": int(p.X.nbytes + p.B.nbytes), "d2h_bytes_per_step": int(p.B.nbytes),
+            "api": "ap_solve_host (host buffers, page-locked)", "steps": e2e_steps},
         "gpu_launches": launches,
         "clocks": clocks,
         "time_to_tol_small": ttt,
@@ -453,6 +556,38 @@ def roofline(p, args, t_launch: float, units: float, sm_max: float, sfu=(32.0, 1
             "tensor_flops_per_entry": tensor_flops}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_time_to_tol_small() -> dict:
+    """The FP64 oracle's own time-to-tolerance on n = 4096, d = 8, RBF l = 0.5,
+    noise 0.1, blocks of 512, tol 1e-6 (every column), measured outright."""
+    import oracle
+    p = wl.small_rbf()
+    t0 = time.perf_counter()
+    r = oracle.ap_solve(oracle.Hyper.of(p), p.X.astype(np.float64), p.B.astype(np.float64), p.block,
+                        stop=oracle.STOP_MAX_REL, tol=p.tol, min_epochs=11, max_epochs=100000)
+    return {"workload": "small_rbf n=4096 d=8 b=512 c=1 tol=1e-6", "time_to_tol_s": time.perf_counter() - t0,
+            "epochs": r.epochs, "converged": r.status == oracle.OK, "rel_res": float(r.rel[0]),
+            "cores": oracle.num_threads()}
+
+
 def cpu_baseline(p, epochs: int, args) -> dict:
     """The FP64 oracle as it stands on the host cores, on a bounded sample of the
     same workload: one AP residual update over a row sample (the hot loop of
@@ -480,7 +615,7 @@ def cpu_baseline(p, epochs: int, args) -> dict:
     entries = float(p.n) * b + steps * float(p.n) * b + float(p.n) ** 2
     t_total = m * t_chol + (steps * float(p.n) * b + float(p.n) ** 2) / ent_per_s
     return {"value": entries / t_total, "unit": "kernel-entries/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
+            "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"one residual update (Eq. text_update_of_r) over {rows} of {p.n} rows x b={b} "
                       f"({t_upd:.1f} s) + FP64 Cholesky of one {b}x{b} block ({t_chol:.1f} s); "
                       f"time-to-tol extrapolated to {m} blocks and {epochs} epochs = {t_total:.0f} s",
@@ -507,7 +642,7 @@ def run_reference(args, rank: int, world: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded NumPy PCG64)", "config": describe(p, args),
         "cpu_baseline": {"value": v, "unit": "kernel-entries/s", "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": timed[-1]["sample"]},
+                         "cpu_model": cpu_model(), "kind": "oracle", "sample": timed[-1]["sample"]},
         "e2e": {"value": v, "unit": "kernel-entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": t_all,
     }
@@ -515,39 +650,10 @@ def run_reference(args, rank: int, world: int):
 
 
 def run_serving(args) -> None:
-    """Replay the serving workload: Poisson arrivals at `rate`/s, n log-uniform in
-    [2^10, 2^18], d in {3..20}, RBF or Matern-5/2, tolerance 1e-2 or 1e-4, half of
-    the requests in the tensor-core form; each request = solve + posterior mean
-    on 1024 test points; admitted by a 120 GB HBM budget."""
+    """The full serving replay (`--serve`): 512 requests by default."""
     import paper_2310_17137_gb300 as ap
-    trace = wl.serving_trace(n_requests=args.serve_requests, rate=args.serve_rate)
-    data = [wl.request_data(r, m_test=1024) for r in trace]
-    srv = ap.ApServer(hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
-    t0 = time.perf_counter()
-    ids = []
-    for r, (X, y, Xt) in zip(trace, data):
-        delay = r.arrival_s - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        h = ap.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise, 0.0)
-        prec = ap.AP_BF16_REFINE if r.low_precision else ap.AP_FP32
-        ids.append(srv.submit(X, y, Xt, h, block=min(r.n, 4096), tol=r.tol, stop=ap.AP_STOP_Y_REL, min_epochs=1,
-                              max_epochs=args.serve_max_epochs, precision=prec))
-    res = [srv.wait(i, timeout_s=3600.0) for i in ids]
-    wall = time.perf_counter() - t0
-    srv.close()
-    lat = np.array([x["latency_s"] for x in res])
-    entries = sum(float(r.n) ** 2 * max(1, x["epochs"]) for r, x in zip(trace, res))
-    line = {"metric": METRIC, "mode": "serving", "value": len(res) / wall, "unit": "solves/s",
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_queue_s": float(np.mean([x["queue_s"] for x in res])), "wall_s": wall,
-            "requests": len(res), "converged": int(sum(x["status"] == ap.AP_OK for x in res)),
-            "kernel_entries_per_s": entries / wall,
-            "config": {"workload": f"{len(res)} requests, Poisson {args.serve_rate}/s, n logU[2^10, 2^18], "
-                                   "d U{3..20}, RBF or Matern-5/2, tol {1e-2, 1e-4}, solve + mean on 1024 "
-                                   "test points, half in the tensor-core form",
-                       "hbm_budget_gb": args.serve_budget_gb, "slots": args.serve_slots,
-                       "max_epochs": args.serve_max_epochs, "stop": "y column"}}
+    out = serving_replay(ap, args, args.serve_requests, args.serve_max_epochs)
+    line = {"metric": METRIC, "mode": "serving", "value": out["solves_per_s"], "unit": "solves/s", **out}
     print(json.dumps(line), flush=True)
 
 
@@ -621,6 +727,15 @@ def main():
     ap_.add_argument("--no-e2e", action="store_true")
     ap_.add_argument("--no-ttt", action="store_true")
     ap_.add_argument("--no-mll", action="store_true", help="skip the MLL-gradient timing")
+    ap_.add_argument("--no-ttt-large", action="store_true",
+                     help="skip the time-to-tolerance runs on the n = 2,097,152 RBF workload")
+    ap_.add_argument("--ttt-large-max-epochs", type=int, default=400)
+    ap_.add_argument("--no-serve-replay", action="store_true", help="skip the reduced serving replay")
+    ap_.add_argument("--serve-replay-requests", type=int, default=48)
+    ap_.add_argument("--time-budget-s", type=float, default=1500.0,
+                     help="skip the time-to-tolerance and serving legs when they would not fit")
+    ap_.add_argument("--compare-steps", type=int, default=3, help="timed steps of the other form")
+    ap_.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end leg")
     ap_.add_argument("--serve", action="store_true", help="replay the serving workload instead")
     ap_.add_argument("--study", action="store_true", help="selection rules and block sizes instead")
     ap_.add_argument("--study-n", type=int, default=65536)
@@ -628,7 +743,7 @@ def main():
     ap_.add_argument("--serve-rate", type=float, default=40.0)
     ap_.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap_.add_argument("--serve-slots", type=int, default=8)
-    ap_.add_argument("--serve-max-epochs", type=int, default=30)
+    ap_.add_argument("--serve-max-epochs", type=int, default=300)
     args = ap_.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

@@ -89,7 +89,11 @@ typedef enum { AP_STOP_MEAN_REL = 0, AP_STOP_MAX_REL = 1, AP_STOP_FRO = 2, AP_ST
 
 /* Arithmetic of the full residual recompute R = B - K_hat W (refinement and
  * certification of the stopping rule, and ap_residual):
- *   AP_RESID_AUTO:        compensated when opts.tol <= 1e-5, plain FP32 otherwise;
+ *   AP_RESID_AUTO:        compensated when opts.tol <= 1e-5, plain FP32 otherwise,
+ *                         switching to compensated for the rest of a solve when the
+ *                         tracked residual meets the rule but a plain FP32
+ *                         recompute does not confirm it (the FP32 sums' own error,
+ *                         about 2^-24 sqrt(n) ||K_hat |W| ||, can exceed tol);
  *   AP_RESID_FP32:        plain FP32 kernel entries and sums;
  *   AP_RESID_COMPENSATED: double-float FP32 (error-free transformations), kernel
  *                         entries to ~1e-11 relative; about 10x the cost. */
@@ -141,6 +145,13 @@ typedef struct ap_opts {
     const volatile int32_t* cancel; /* optional host flag: when it reads non-zero at the end of an
                                        epoch, ap_solve / ap_mll_grad stop with AP_ERR_CANCELLED
                                        (W holds the last iterate) */
+    int32_t escalate;     /* low-precision forms: 1 (default) = run the remaining epochs with the
+                             FP32 update when a refinement finds that the true residual fell by
+                             less than half of what the tracked one claims since the previous
+                             recompute (the low-precision updates' error, not AP's convergence,
+                             limits progress), or when the tracked residual turns NaN or exceeds
+                             twice the last certified one (divergence: W is rolled back to the
+                             last refinement that lowered the true residual); 0 = never */
 } ap_opts;
 
 /* Report of ap_solve / ap_mll_grad.  rel_res_* hold the first c columns. */
@@ -163,12 +174,16 @@ typedef struct ap_info {
     double t_update_s;                    /* opts.profile: summed duration of the residual-update kernels */
     int64_t n_update;                     /* opts.profile: number of residual-update launches timed */
     double t_blocksolve_s;                /* opts.profile: summed duration of the block solves */
+    int32_t fp32_epochs;                  /* epochs run with the FP32 update after an escalation */
+    int32_t compensated;                  /* rel_res_true comes from the compensated recompute */
+    int32_t diverged;                     /* the low-precision updates diverged and were rolled back */
 } ap_info;
 
 typedef struct ap_ctx ap_ctx;
 
 /* Fill *o with the defaults: block 4096, GS, MEAN_REL, tol 1, 11..1000 epochs,
- * FP32, refine_every 4, seed 0, default stream, no budget, no trace. */
+ * FP32, refine_every 4, seed 0, default stream, no budget, no trace,
+ * escalation on. */
 void ap_opts_default(ap_opts* o);
 
 /* Create a solver context for the n training inputs X_dev (device, n x d FP32,
@@ -195,6 +210,16 @@ ap_status ap_set_hyper(ap_ctx* ctx, const ap_hyper* h);
  * device wait of the tensor-core update ran out), CUDA. */
 ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_dev,
                    float* W_dev, ap_info* info);
+
+/* One-shot solve for host-resident data: copies X_host (n x d) and B_host
+ * (n x c) to the device, builds the context (ap_create: the Cholesky cache),
+ * runs ap_solve (opts as for ap_create/ap_solve; W0 none), copies W to W_host
+ * (n x c) and releases everything, all on opts.stream.  Page-locked host
+ * buffers give full-bandwidth copies; pageable ones work too.  info (may be
+ * NULL) as for ap_solve.  Returns ap_create's or ap_solve's status; W_host is
+ * written whenever ap_solve wrote W. */
+ap_status ap_solve_host(const float* X_host, int64_t n, int32_t d, const ap_hyper* h, const ap_opts* o,
+                        const float* B_host, int32_t c, float* W_host, ap_info* info);
 
 /* True residual R = B - K_hat W (n x c, device), FP32 form, all n^2 kernel
  * entries evaluated on the fly (the residual lemma of App. B).  Used for
@@ -346,6 +371,7 @@ typedef struct ap_request_result {
     double latency_s;         /* submit -> result written */
     size_t reserved_bytes;    /* HBM reserved for the request while it runs */
     int32_t started;          /* 1 once a worker has taken the request */
+    int32_t compensated;      /* rel_res comes from the compensated recompute */
 } ap_request_result;
 
 /* Start a server on device `device` with `slots` worker streams and an HBM

@@ -28,7 +28,7 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_ERR_CANCELLED, AP_BF16_REFINE, AP_E
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ap_tracked_residual", "ap_device_bytes", "ApServer",
+           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ap_tracked_residual", "ap_device_bytes", "ap_solve_host", "ApServer",
            "MLLDataFit"]
 
 
@@ -139,7 +139,8 @@ def info_dict(info: _capi.ap_info) -> dict:
                 t_cache_s=info.t_cache_s, t_solve_s=info.t_solve_s, t_refine_s=info.t_refine_s,
                 kernel_entries=info.kernel_entries, entries_per_s=info.entries_per_s,
                 gpu_launches=info.gpu_launches, data_fit=info.data_fit, t_update_s=info.t_update_s,
-                n_update=info.n_update, t_blocksolve_s=info.t_blocksolve_s)
+                n_update=info.n_update, t_blocksolve_s=info.t_blocksolve_s, fp32_epochs=info.fp32_epochs,
+                compensated=bool(info.compensated), diverged=int(info.diverged))
 
 
 def ap_solve(ctx: Context, B, W0=None, W=None):
@@ -157,6 +158,24 @@ def ap_solve(ctx: Context, B, W0=None, W=None):
     if ctx._trace is not None:
         trace = np.frombuffer(ctx._trace, dtype=np.int32)[:min(info.steps, ctx.opts.trace_cap)].copy()
     return st, W, info_dict(info), trace
+
+
+def ap_solve_host(X: np.ndarray, B: np.ndarray, hyper: Hyper, opts=None, W: Optional[np.ndarray] = None):
+    """One-shot solve for host arrays (float32, C-contiguous; page-locked memory
+    such as a pinned torch tensor's numpy view copies fastest): copies in,
+    builds the cache, runs Alg. 1, copies W out.  Returns (status, W, info)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    B2 = np.ascontiguousarray(B, dtype=np.float32).reshape(X.shape[0], -1)
+    if W is None:
+        W = np.empty_like(B2)
+    opts = opts or ap_opts_default()
+    h, ell = hyper.to_c()
+    info = _capi.ap_info()
+    st = _capi.load().ap_solve_host(X.ctypes.data, X.shape[0], X.shape[1], ctypes.byref(h), ctypes.byref(opts),
+                                    B2.ctypes.data, B2.shape[1], W.ctypes.data, ctypes.byref(info))
+    if st not in (AP_OK, AP_ERR_NOT_CONVERGED):
+        raise ApError(st, "ap_solve_host")
+    return st, W, info_dict(info)
 
 
 def ap_residual(ctx: Context, B, W, R=None):
@@ -304,7 +323,7 @@ class ApServer:
     def _res(res) -> dict:
         return dict(done=bool(res.done), status=res.status, epochs=res.epochs, rel_res=res.rel_res,
                     queue_s=res.queue_s, latency_s=res.latency_s, reserved_bytes=res.reserved_bytes,
-                    started=bool(res.started))
+                    started=bool(res.started), compensated=bool(res.compensated))
 
     def cancel(self, rid: int) -> None:
         """Drop a queued request, or stop a running one at the end of its epoch."""

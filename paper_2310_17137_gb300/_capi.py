@@ -28,7 +28,7 @@ EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_resid
            "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval",
            "ap_grad_quadforms_static", "ap_server_create", "ap_server_submit", "ap_server_poll",
            "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result",
-           "ap_tracked_residual", "ap_device_bytes", "ap_last_cuda_error", "ap_server_cancel"]
+           "ap_tracked_residual", "ap_device_bytes", "ap_last_cuda_error", "ap_server_cancel", "ap_solve_host"]
 
 
 class ap_hyper(ctypes.Structure):
@@ -44,7 +44,8 @@ class ap_opts(ctypes.Structure):
                 ("hbm_budget", ctypes.c_size_t), ("block_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("trace_cap", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("residual_mode", ctypes.c_int32), ("cache_gemm", ctypes.c_int32),
-                ("wait_limit_cycles", ctypes.c_int64), ("cancel", ctypes.c_void_p)]
+                ("wait_limit_cycles", ctypes.c_int64), ("cancel", ctypes.c_void_p),
+                ("escalate", ctypes.c_int32)]
 
 
 class ap_info(ctypes.Structure):
@@ -56,7 +57,8 @@ class ap_info(ctypes.Structure):
                 ("t_refine_s", ctypes.c_double), ("kernel_entries", ctypes.c_double),
                 ("entries_per_s", ctypes.c_double), ("gpu_launches", ctypes.c_int64),
                 ("data_fit", ctypes.c_double), ("t_update_s", ctypes.c_double),
-                ("n_update", ctypes.c_int64), ("t_blocksolve_s", ctypes.c_double)]
+                ("n_update", ctypes.c_int64), ("t_blocksolve_s", ctypes.c_double),
+                ("fp32_epochs", ctypes.c_int32), ("compensated", ctypes.c_int32), ("diverged", ctypes.c_int32)]
 
 
 class ap_request(ctypes.Structure):
@@ -70,7 +72,8 @@ class ap_request(ctypes.Structure):
 class ap_request_result(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int), ("epochs", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double),
-                ("reserved_bytes", ctypes.c_size_t), ("started", ctypes.c_int32)]
+                ("reserved_bytes", ctypes.c_size_t), ("started", ctypes.c_int32),
+                ("compensated", ctypes.c_int32)]
 
 
 _lib = None
@@ -99,6 +102,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_set_hyper": (st, [P, ctypes.POINTER(ap_hyper)]),
         "ap_solve": (st, [P, P, i32, P, P, ctypes.POINTER(ap_info)]),
         "ap_residual": (st, [P, P, i32, P, P]),
+        "ap_solve_host": (st, [P, i64, i32, ctypes.POINTER(ap_hyper), ctypes.POINTER(ap_opts), P, i32, P,
+                               ctypes.POINTER(ap_info)]),
         "ap_predict_mean": (st, [P, P, P, i64, P]),
         "ap_grad_quadforms": (st, [P, P, P, i32, P, P]),
         "ap_grad_quadforms_static": (st, [P, P, P, i32, P, P]),

@@ -13,9 +13,24 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ap_internal.cuh"
 
 using namespace ap;
+
+namespace {
+// Named host-side range of one phase (cache, solve, epoch, refinement,
+// prediction, gradient) for profilers and timeline tools; free when no tool
+// is attached.
+class PhaseRange {
+   public:
+    explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+    PhaseRange(const PhaseRange&) = delete;
+    PhaseRange& operator=(const PhaseRange&) = delete;
+};
+}  // namespace
 
 struct ap_ctx {
     int device = 0;  // current device at ap_create; every call runs with it current
@@ -41,6 +56,7 @@ struct ap_ctx {
     // per-solve buffers (stride Cp)
     int Cp = 0;
     float *R = nullptr, *W = nullptr, *Bp = nullptr, *Z = nullptr, *Delta = nullptr, *Tmp = nullptr;
+    float* W_ckpt = nullptr;  // low-precision forms: W at the last refinement that lowered the true residual
     double *part_norm = nullptr, *part_col = nullptr;
     int64_t part_alloc = 0;
     // block-solve work split and partial sums
@@ -68,6 +84,8 @@ struct ap_ctx {
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
     // tensor-core form (AP_BF16_REFINE)
     bool tc = false;
+    bool tc_steps = false;  // the current solve's steps use the tensor-core update (false after escalation)
+    bool graph_tc = false;  // form of the steps in the captured epoch graph
     int kd = 16, cpb = 0, num_sms = 152;
     int64_t tps128 = 0;
     uint8_t *XA = nullptr, *XB = nullptr, *DT = nullptr;
@@ -76,6 +94,9 @@ struct ap_ctx {
     int* tc_err = nullptr;
     int64_t launches = 0;
     int r_tracked_c = 0;  // c of the solve whose residual R holds (0: none)
+    int divergences = 0;  // low-precision runs rolled back to a checkpoint (this solve)
+    bool comp_auto = false;  // AP_RESID_AUTO switched this solve's recomputes to the compensated form
+    bool comp_used = false;  // the last recompute was compensated
     cudaError_t last_cuda = cudaSuccess;
 };
 
@@ -242,10 +263,11 @@ ap_status prep_inputs(ap_ctx* ctx, const float* X, int64_t n, float* out, float*
 bool use_compensated(const ap_ctx* ctx) {
     if (ctx->o.residual_mode == AP_RESID_COMPENSATED) return true;
     if (ctx->o.residual_mode == AP_RESID_FP32) return false;
-    return ctx->o.tol <= 1e-5;
+    return ctx->o.tol <= 1e-5 || ctx->comp_auto;
 }
 
 ap_status build_cache(ap_ctx* ctx) {
+    PhaseRange range("ap: Cholesky cache (prep, K_II, FP64 factor, inverse)");
     drop_graph(ctx);
     AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
     AP_TRY(prep_inputs(ctx, ctx->X, ctx->n, ctx->Xs, ctx->Xs_lo));
@@ -356,6 +378,7 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         dfree(ctx, ctx->Z);
         dfree(ctx, ctx->Delta);
         dfree(ctx, ctx->Tmp);
+        dfree(ctx, ctx->W_ckpt);
         dfree(ctx, ctx->part_col);
         dfree(ctx, ctx->spart);
         dfree(ctx, ctx->sticket);
@@ -366,6 +389,7 @@ ap_status ensure_solve(ap_ctx* ctx, int Cp) {
         AP_TRY(dalloc_t(ctx, &ctx->W, nc));
         AP_TRY(dalloc_t(ctx, &ctx->Bp, nc));
         AP_TRY(dalloc_t(ctx, &ctx->Tmp, nc));
+        if (ctx->tc) AP_TRY(dalloc_t(ctx, &ctx->W_ckpt, nc));
         AP_TRY(dalloc_t(ctx, &ctx->Z, (size_t)ctx->nt * kTile * Cp));
         AP_TRY(dalloc_t(ctx, &ctx->Delta, (size_t)ctx->b * Cp));
         block_solve_layout(ctx->nt, ctx->num_sms, &ctx->sol_tpc, &ctx->sol_maxj);
@@ -422,7 +446,7 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
     sp.spart = ctx->spart;
     sp.sticket = ctx->sticket;
     AP_CK(launch_block_solve(sp, ctx->st, &ctx->launches));
-    if (ctx->tc) {
+    if (ctx->tc_steps) {
         AP_CK(launch_tc_pack_delta(ctx->Delta, ctx->b, Cp, ctx->cpb, ctx->DT, ctx->st));
         ++ctx->launches;
     }
@@ -430,7 +454,7 @@ ap_status launch_step(ap_ctx* ctx, bool colnorms, int64_t j) {
         AP_CK(cudaEventRecordWithFlags(ctx->ev_bs[2 * j + 1], ctx->st, rec_flags));
         AP_CK(cudaEventRecordWithFlags(ctx->ev_up[2 * j], ctx->st, rec_flags));
     }
-    if (ctx->tc) {
+    if (ctx->tc_steps) {
         Shape sh;
         sh.rows = 128;
         sh.tps = ctx->tps128;
@@ -498,7 +522,9 @@ void collect_profile(ap_ctx* ctx, int64_t steps) {
 
 // out = base - K_hat V over all n columns (the FP32 residual recompute).
 ap_status launch_full_residual(ap_ctx* ctx, const float* base, const float* V, float* out, int flags) {
+    PhaseRange range("ap: residual recompute R = B - K_hat W");
     const bool comp = use_compensated(ctx);
+    ctx->comp_used = comp;
     const Shape sh = comp ? comp_shape(ctx, ctx->n) : step_shape(ctx, ctx->Cp, ctx->n);
     KmvParams kp = {};
     kp.Xa = ctx->Xs;
@@ -543,6 +569,7 @@ ap_status run_epoch(ap_ctx* ctx, int64_t steps) {
                 cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
                 if (s == AP_OK && e == cudaSuccess && g) {
                     if (cudaGraphInstantiate(&ctx->graph, g, 0) != cudaSuccess) ctx->graph = nullptr;
+                    ctx->graph_tc = ctx->tc_steps;
                 }
                 if (g) cudaGraphDestroy(g);
             }
@@ -552,7 +579,7 @@ ap_status run_epoch(ap_ctx* ctx, int64_t steps) {
         }
         if (ctx->graph) {
             AP_CK(cudaGraphLaunch(ctx->graph, ctx->st));
-            ctx->launches += (ctx->tc ? 4 : 3) * steps;
+            ctx->launches += (ctx->tc_steps ? 4 : 3) * steps;
             return AP_OK;
         }
     }
@@ -571,6 +598,20 @@ bool stop_met(int rule, double tol, int c, const double* rel, double fro_r, doub
     double mean = 0.0;
     for (int k = 0; k < c; ++k) mean += rel[k];
     return mean / c < tol;
+}
+
+// The quantity the stopping rule compares with tol, from per-column relative
+// residuals (FRO weights each column by ||b_c||^2).
+double rule_measure(int rule, int c, const double* rel, const double* bn) {
+    if (rule == AP_STOP_Y_REL) return rel[0];
+    double acc = 0.0, w = 0.0;
+    for (int k = 0; k < c; ++k) {
+        if (rule == AP_STOP_MAX_REL) acc = std::max(acc, rel[k]);
+        else if (rule == AP_STOP_FRO) acc += rel[k] * rel[k] * bn[k], w += bn[k];
+        else acc += rel[k];
+    }
+    if (rule == AP_STOP_FRO) return w > 0.0 ? sqrt(acc / w) : sqrt(acc);
+    return rule == AP_STOP_MAX_REL ? acc : acc / c;
 }
 
 ap_status check_hyper(const ap_hyper* h, int d) {
@@ -615,6 +656,7 @@ void free_all(ap_ctx* ctx) {
 int solve_width(const ap_ctx* ctx, int c) { return ctx->tc ? std::max(16, pad_c(c)) : pad_c(c); }
 
 ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev, float* W_dev, ap_info* info) {
+    PhaseRange range("ap: solve (Alg. 1)");
     const int Cp = solve_width(ctx, c);
     AP_TRY(ensure_solve(ctx, Cp));
     const int64_t want_trace = ctx->o.block_trace ? ctx->o.trace_cap : 0;
@@ -627,6 +669,11 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
     }
     const int64_t l0 = ctx->launches;
     ctx->r_tracked_c = 0;
+    ctx->tc_steps = ctx->tc;
+    ctx->comp_auto = false;
+    ctx->divergences = 0;
+    if (ctx->graph && ctx->graph_tc != ctx->tc_steps) drop_graph(ctx);
+    int fp32_epochs = 0;
     AP_TRY(enter(ctx));
     AP_CK(launch_pad_copy(B_dev, ctx->n, c, ctx->Bp, Cp, ctx->st));
     ++ctx->launches;
@@ -649,6 +696,9 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         AP_CK(cudaMemcpyAsync(ctx->R, ctx->Bp, sizeof(float) * ctx->n * Cp, cudaMemcpyDeviceToDevice, ctx->st));
     }
     AP_TRY(launch_norms(ctx, ctx->R, kEpiBlockNorms | kEpiColNorms));
+    AP_CK(cudaMemcpyAsync(rn, ctx->colnorm, sizeof(double) * Cp, cudaMemcpyDeviceToHost, ctx->st));
+    if (ctx->tc)
+        AP_CK(cudaMemcpyAsync(ctx->W_ckpt, ctx->W, sizeof(float) * ctx->n * Cp, cudaMemcpyDeviceToDevice, ctx->st));
     AP_CK(cudaStreamSynchronize(ctx->st));
 
     double rel[AP_MAX_RHS] = {}, rel_true[AP_MAX_RHS] = {};
@@ -670,14 +720,20 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         }
         return epoch >= ctx->o.min_epochs && stop_met(ctx->o.stop, ctx->o.tol, c, out, sqrt(fr), sqrt(fb));
     };
+    // true residual (in the stopping rule's measure) at the start and after the
+    // last refinement: the reference for the escalation test
+    rel_from(rel_true);
+    double true_prev = rule_measure(ctx->o.stop, c, rel_true, bn);
     AP_CK(cudaEventRecord(ctx->ev_a, ctx->st));
     while (true) {
         int64_t ns = ctx->m;
         if (ctx->o.max_steps > 0) ns = std::min<int64_t>(ns, ctx->o.max_steps - steps);
         if (ns <= 0) break;
+        PhaseRange epoch_range(ctx->tc_steps ? "ap: epoch (tensor-core update)" : "ap: epoch (FP32 update)");
         AP_TRY(run_epoch(ctx, ns));
         steps += ns;
         ++epoch;
+        if (ctx->tc && !ctx->tc_steps) ++fp32_epochs;
         int nanf = 0, tcerr = 0;
         AP_CK(cudaMemcpyAsync(rn, ctx->colnorm, sizeof(double) * Cp, cudaMemcpyDeviceToHost, ctx->st));
         AP_CK(cudaMemcpyAsync(&nanf, ctx->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -688,12 +744,38 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
             status = AP_ERR_TIMEOUT;
             break;
         }
+        bool met = rel_from(rel);
+        // Divergence of the low-precision updates (their kernel-entry error can
+        // exceed what sigma^2 keeps positive definite: large n, small noise,
+        // smooth kernels): a NaN, or a tracked residual above twice the last
+        // certified one.  Roll W back to the last checkpoint, recompute R and
+        // continue with the FP32 update.
+        if (ctx->tc_steps && ctx->o.escalate && (nanf || !(rule_measure(ctx->o.stop, c, rel, bn) <= 2.0 * true_prev))) {
+            ctx->tc_steps = false;
+            drop_graph(ctx);
+            AP_CK(cudaMemcpyAsync(ctx->W, ctx->W_ckpt, sizeof(float) * ctx->n * Cp, cudaMemcpyDeviceToDevice, ctx->st));
+            AP_CK(cudaMemsetAsync(ctx->nan_flag, 0, sizeof(int), ctx->st));
+            AP_CK(cudaEventRecord(ctx->ev_r0, ctx->st));
+            AP_TRY(launch_full_residual(ctx, ctx->Bp, ctx->W, ctx->R, kEpiBlockNorms | kEpiColNorms));
+            AP_CK(cudaEventRecord(ctx->ev_r1, ctx->st));
+            AP_CK(cudaMemcpyAsync(rn, ctx->colnorm, sizeof(double) * Cp, cudaMemcpyDeviceToHost, ctx->st));
+            AP_CK(cudaMemcpyAsync(&nanf, ctx->nan_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+            AP_CK(cudaStreamSynchronize(ctx->st));
+            float rms = 0.f;
+            cudaEventElapsedTime(&rms, ctx->ev_r0, ctx->ev_r1);
+            t_refine += rms * 1e-3;
+            ++refinements;
+            ++ctx->divergences;
+            met = rel_from(rel);
+            have_true = true;
+            for (int k = 0; k < c; ++k) rel_true[k] = rel[k];
+            true_prev = rule_measure(ctx->o.stop, c, rel, bn);
+        }
         if (nanf) {
             status = AP_ERR_NAN;
             break;
         }
-        bool met = rel_from(rel);
-        const bool periodic = low_precision && ctx->o.refine_every > 0 && epoch % ctx->o.refine_every == 0;
+        const bool periodic = ctx->tc_steps && ctx->o.refine_every > 0 && epoch % ctx->o.refine_every == 0;
         if (met || periodic) {
             // Refinement / certification: recompute R = B - K_hat W over all n^2
             // entries in the FP32 form (residual lemma, App. B) and continue
@@ -712,8 +794,28 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
                 status = AP_ERR_NAN;
                 break;
             }
+            const double tracked_now = rule_measure(ctx->o.stop, c, rel, bn);
+            const bool tracked_met = met;
             met = rel_from(rel_true);
             have_true = true;
+            // The tracked rule held but the plain FP32 recompute does not confirm
+            // it: when K_hat |W| is much larger than B the FP32 sums' own error can
+            // exceed tol, so AP_RESID_AUTO certifies with the compensated recompute
+            // from here on (refinement then continues from an accurate residual)
+            if (tracked_met && !met && !ctx->comp_used && ctx->o.residual_mode == AP_RESID_AUTO)
+                ctx->comp_auto = true;
+            // Escalation: when the true residual fell by less than half of what
+            // the tracked one claims since the last recompute, the low-precision
+            // updates' own error, not AP's rate, limits progress
+            const double true_now = rule_measure(ctx->o.stop, c, rel_true, bn);
+            if (!met && ctx->tc_steps && ctx->o.escalate && true_prev - true_now < 0.5 * (true_prev - tracked_now)) {
+                ctx->tc_steps = false;
+                drop_graph(ctx);
+            }
+            if (ctx->tc_steps && true_now <= true_prev)
+                AP_CK(cudaMemcpyAsync(ctx->W_ckpt, ctx->W, sizeof(float) * ctx->n * Cp, cudaMemcpyDeviceToDevice,
+                                      ctx->st));
+            true_prev = true_now;
             for (int k = 0; k < c; ++k) rel[k] = rel_true[k];
         }
         if (met) {
@@ -777,6 +879,9 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
         info->t_update_s = ctx->t_update;
         info->n_update = ctx->n_update;
         info->t_blocksolve_s = ctx->t_bsolve;
+        info->fp32_epochs = fp32_epochs;
+        info->compensated = ctx->comp_used && have_true ? 1 : 0;
+        info->diverged = ctx->divergences;
     }
     return status;
 }
@@ -828,6 +933,9 @@ void ap_opts_default(ap_opts* o) {
     o->profile = 0;
     o->residual_mode = AP_RESID_AUTO;
     o->cache_gemm = AP_CACHE_TC_EXACT;
+    o->wait_limit_cycles = 0;
+    o->cancel = nullptr;
+    o->escalate = 1;
 }
 
 size_t ap_sizeof_opts(void) { return sizeof(ap_opts); }
@@ -965,6 +1073,46 @@ ap_status ap_solve(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W0_d
     return s;
 }
 
+ap_status ap_solve_host(const float* X_host, int64_t n, int32_t d, const ap_hyper* h, const ap_opts* o,
+                        const float* B_host, int32_t c, float* W_host, ap_info* info) {
+    if (!X_host || !B_host || !W_host || !h || !o || n < 1 || d < 1 || d > AP_MAX_DIM || c < 1 || c > AP_MAX_RHS)
+        return AP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)o->stream;
+    const size_t xb = sizeof(float) * (size_t)n * (size_t)d, bb = sizeof(float) * (size_t)n * (size_t)c;
+    float *X = nullptr, *B = nullptr, *W = nullptr;
+    auto release = [&]() {
+        cudaFreeAsync(X, st);
+        cudaFreeAsync(B, st);
+        cudaFreeAsync(W, st);
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+    };
+    if (cudaMallocAsync((void**)&X, xb, st) != cudaSuccess || cudaMallocAsync((void**)&B, bb, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&W, bb, st) != cudaSuccess) {
+        release();
+        return AP_ERR_NOMEM;
+    }
+    if (cudaMemcpyAsync(X, X_host, xb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(B, B_host, bb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        release();
+        return AP_ERR_CUDA;
+    }
+    ap_ctx* ctx = nullptr;
+    ap_status s = ap_create(&ctx, X, n, d, h, o);
+    if (s != AP_OK) {
+        release();
+        return s;
+    }
+    s = ap_solve(ctx, B, c, nullptr, W, info);
+    const bool wrote = s == AP_OK || s == AP_ERR_NOT_CONVERGED || s == AP_ERR_CANCELLED;
+    if (wrote && (cudaMemcpyAsync(W_host, W, bb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                  cudaStreamSynchronize(st) != cudaSuccess))
+        s = AP_ERR_CUDA;
+    ap_destroy(ctx);
+    release();
+    return s;
+}
+
 ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W_dev, float* R_dev) {
     if (!ctx || !B_dev || !W_dev || !R_dev || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
     AP_DEVICE_GUARD(ctx);
@@ -982,6 +1130,7 @@ ap_status ap_residual(ap_ctx* ctx, const float* B_dev, int32_t c, const float* W
 }
 
 ap_status ap_predict_mean(ap_ctx* ctx, const float* w_dev, const float* Xs_dev, int64_t M, float* mean_dev) {
+    PhaseRange range("ap: posterior mean");
     if (!ctx || !w_dev || !Xs_dev || !mean_dev || M < 1) return AP_ERR_INVALID_ARG;
     AP_DEVICE_GUARD(ctx);
     if (M > ctx->Xt_alloc) {
@@ -1062,6 +1211,7 @@ static ap_status grad_quadforms_impl(ap_ctx* ctx, const float* U, const float* V
 
 ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev, int32_t c, const double* alpha_host,
                             double* out_host) {
+    PhaseRange range("ap: gradient quadratic forms");
     if (!ctx || !U_dev || !V_dev || !alpha_host || !out_host || c < 1 || c > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
     AP_DEVICE_GUARD(ctx);
     const int Cp = pad_c(c);
@@ -1076,6 +1226,7 @@ ap_status ap_grad_quadforms(ap_ctx* ctx, const float* U_dev, const float* V_dev,
 
 ap_status ap_mll_grad(ap_ctx* ctx, const float* y_dev, int32_t n_probes, const float* Z_dev, float* grad_host,
                       ap_info* info) {
+    PhaseRange range("ap: MLL gradient");
     if (!ctx || !y_dev || !grad_host || n_probes < 0 || n_probes + 1 > AP_MAX_RHS) return AP_ERR_INVALID_ARG;
     AP_DEVICE_GUARD(ctx);
     const int l = n_probes, c = l + 1;

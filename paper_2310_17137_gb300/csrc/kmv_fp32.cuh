@@ -200,9 +200,25 @@ __device__ __forceinline__ void epi_ticket(const EpiParams& e, double* red_d, in
     }
 }
 
+// With C a multiple of 4 the distance and the contraction run as packed FP32
+// pairs (fma.rn.f32x2: one instruction for two lanes, each rounded as the scalar
+// operation): the squared distance over pairs of coordinates (two partial sums,
+// added at the end), the contraction over pairs of right-hand sides.  Shared
+// memory holds the operands exactly as in the scalar form.
+template <int C>
+struct KmvPaired {
+    static constexpr bool value = C % 4 == 0;
+};
+
+template <int D, int C, int RM>
+constexpr size_t kmv_smem_floats() {
+    return (size_t)kKmvTN * (D + C) + (size_t)kKmvThreads * RM * C;
+}
+
 template <int KERN, int D, int C, int RM>
-__global__ void __launch_bounds__(kKmvThreads) kmv_fp32_kernel(const KmvParams p) {
+__global__ void __launch_bounds__(kKmvThreads, 4) kmv_fp32_kernel(const KmvParams p) {
     constexpr int ROWS = kKmvThreads * RM;
+    constexpr bool kPaired = KmvPaired<C>::value;
     extern __shared__ float4 kmv_smem4[];
     float* s_xb = reinterpret_cast<float*>(kmv_smem4);  // kKmvTN * D
     float* s_v = s_xb + kKmvTN * D;                     // kKmvTN * C
@@ -252,6 +268,68 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_fp32_kernel(const KmvParams p
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[q][c] = 0.0f;
 
+    if constexpr (kPaired) {
+        float2 xa2[RM][D / 2], acc2[RM][C / 2];
+#pragma unroll
+        for (int q = 0; q < RM; ++q) {
+#pragma unroll
+            for (int k = 0; k < D / 2; ++k) xa2[q][k] = make_float2(xa[q][2 * k], xa[q][2 * k + 1]);
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c) acc2[q][c] = make_float2(0.0f, 0.0f);
+        }
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        for (int64_t cb = c_lo; cb < c_hi; cb += kKmvTN) {
+            const int cnt = (int)min((int64_t)kKmvTN, c_hi - cb);
+            __syncthreads();
+            {
+                const float4* gx = reinterpret_cast<const float4*>(p.Xb + cb * D);
+                float4* sx = reinterpret_cast<float4*>(s_xb);
+                for (int t = tid; t < cnt * D / 4; t += kKmvThreads) sx[t] = __ldg(gx + t);
+                const float4* gv4 = reinterpret_cast<const float4*>(p.V + (cb - col0) * C);
+                float4* sv4 = reinterpret_cast<float4*>(s_v);
+                for (int t = tid; t < cnt * C / 4; t += kKmvThreads) sv4[t] = __ldg(gv4 + t);
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int jj = 0; jj < cnt; ++jj) {
+                float2 xb2[D / 2];
+#pragma unroll
+                for (int k4 = 0; k4 < D / 4; ++k4) {
+                    const float4 v = reinterpret_cast<const float4*>(s_xb + jj * D)[k4];
+                    xb2[2 * k4] = make_float2(v.x, v.y);
+                    xb2[2 * k4 + 1] = make_float2(v.z, v.w);
+                }
+                float kv[RM];
+#pragma unroll
+                for (int q = 0; q < RM; ++q) {
+                    float2 tp = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int k = 0; k < D / 2; ++k) {
+                        const float2 df = __ffma2_rn(xb2[k], m1, xa2[q][k]);  // xa - xb, exact negation
+                        tp = __ffma2_rn(df, df, tp);
+                    }
+                    kv[q] = phi_fp32<KERN>(tp.x + tp.y);
+                }
+#pragma unroll
+                for (int c4 = 0; c4 < C / 4; ++c4) {
+                    const float4 v = reinterpret_cast<const float4*>(s_v + jj * C)[c4];
+#pragma unroll
+                    for (int q = 0; q < RM; ++q) {
+                        const float2 kd = make_float2(kv[q], kv[q]);
+                        acc2[q][2 * c4] = __ffma2_rn(kd, make_float2(v.x, v.y), acc2[q][2 * c4]);
+                        acc2[q][2 * c4 + 1] = __ffma2_rn(kd, make_float2(v.z, v.w), acc2[q][2 * c4 + 1]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RM; ++q)
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c) {
+                acc[q][2 * c] = acc2[q][c].x;
+                acc[q][2 * c + 1] = acc2[q][c].y;
+            }
+    } else
     for (int64_t cb = c_lo; cb < c_hi; cb += kKmvTN) {
         const int cnt = (int)min((int64_t)kKmvTN, c_hi - cb);
         __syncthreads();
@@ -380,8 +458,7 @@ inline int rows_per_thread(int D, int C) {
 template <int KERN, int D, int C>
 cudaError_t launch_kmv_inst(const KmvParams& p, cudaStream_t st) {
     constexpr int RM = (D + C <= 20) ? 4 : ((D + C <= 36) ? 2 : 1);
-    constexpr int ROWS = kKmvThreads * RM;
-    const size_t smem = sizeof(float) * ((size_t)kKmvTN * (D + C) + (size_t)ROWS * C);
+    const size_t smem = sizeof(float) * kmv_smem_floats<D, C, RM>();
     auto fn = kmv_fp32_kernel<KERN, D, C, RM>;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -42,6 +42,7 @@ struct Job {
     ap_status status = AP_OK;
     int epochs = 0;
     double rel_res = 0.0;
+    int compensated = 0;
     bool done = false;
     volatile int32_t cancel = 0;  // read by the solve between epochs
 };
@@ -152,6 +153,7 @@ ap_status run_job(ap_server* srv, Job* j, cudaStream_t st) {
     s = j->cancel ? AP_ERR_CANCELLED : ap_solve(ctx, B, 1, nullptr, W, &info);
     j->epochs = info.epochs;
     j->rel_res = info.rel_res_true[0];
+    j->compensated = info.compensated;
     if (s == AP_OK || s == AP_ERR_NOT_CONVERGED) {
         ap_status sp = ap_predict_mean(ctx, W, Xt, r.M, mu);
         if (sp != AP_OK) s = sp;
@@ -284,6 +286,7 @@ ap_status ap_server_poll(ap_server* srv, int64_t id, ap_request_result* res) {
     res->latency_s = j->done ? j->t_done - j->t_submit : 0.0;
     res->reserved_bytes = j->reserve;
     res->started = j->t_start > 0 ? 1 : 0;
+    res->compensated = j->compensated;
     return AP_OK;
 }
 

@@ -106,3 +106,37 @@ def test_cancel_flag_stops_a_solve_between_epochs(prec):
     assert not th.is_alive()
     assert "err" in out and out["err"].status == ap.AP_ERR_CANCELLED
     ap.ap_destroy(ctx)
+
+
+def test_low_precision_divergence_is_rolled_back():
+    # Request 6 of the 64-request serving trace: n = 222,057 points in [0, 1]^3,
+    # RBF with a lengthscale of 0.31 and outputscale 2, noise 9.5e-3.  Its
+    # tensor-core updates diverged to NaN in ten epochs: the FP16 hi/lo distance
+    # error grows with |z|^2, and summed over the many near neighbours of each
+    # row it outweighs sigma^2, so the perturbed operator is not positive
+    # definite.  The solver must detect the divergence, roll W back to its last
+    # checkpoint and continue with the FP32 update: no NaN, and the certified
+    # residual never above the starting one.
+    r = wl.serving_trace(n_requests=64, rate=40.0)[6]
+    assert (r.n, r.d, r.kernel, r.low_precision) == (222057, 3, wl.RBF, True)
+    X, y, _ = wl.request_data(r, m_test=16)
+    ctx = ap.ap_create(_t(X), ap.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise, 0.0),
+                       ap.ap_opts_default(block=4096, precision=ap.AP_BF16_REFINE, tol=r.tol, stop=ap.AP_STOP_Y_REL,
+                                          min_epochs=1, max_epochs=40, refine_every=4))
+    st, W, info, _ = ap.ap_solve(ctx, _t(y))
+    ap.ap_destroy(ctx)
+    # the FP32 form alone on the same request, for as many epochs as the rolled-back run had left
+    ctx32 = ap.ap_create(_t(X), ap.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise, 0.0),
+                         ap.ap_opts_default(block=4096, precision=ap.AP_FP32, tol=r.tol, stop=ap.AP_STOP_Y_REL,
+                                            min_epochs=1, max_epochs=max(1, info["fp32_epochs"])))
+    st32, _, info32, _ = ap.ap_solve(ctx32, _t(y))
+    ap.ap_destroy(ctx32)
+    print(f"status {ap.ap_status_str(st)}, diverged {info['diverged']}, fp32 epochs {info['fp32_epochs']}, "
+          f"rel_res_true {info['rel_res_true'][0]:.6e}; FP32 form alone: {ap.ap_status_str(st32)}, "
+          f"rel_res_true {info32['rel_res_true'][0]:.6e}")
+    assert st in (ap.AP_OK, ap.AP_ERR_NOT_CONVERGED)
+    assert info["diverged"] >= 1 and info["fp32_epochs"] >= 1
+    assert np.all(np.isfinite(W.cpu().numpy()))
+    # after the roll-back the run is the FP32 form's: no worse than FP32 alone
+    # over the same epochs (up to the noise of their different starting points)
+    assert info["rel_res_true"][0] <= max(1.0 + 1e-6, 1.5 * info32["rel_res_true"][0])

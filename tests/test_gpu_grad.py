@@ -38,7 +38,8 @@ def test_mll_grad_n4096_matern32_31_probes_against_oracle():
     Z = np.ascontiguousarray(p.B[:, 1:])
     h = oracle.Hyper.of(p)
     X64, B64, Z64 = p.X.astype(np.float64), p.B.astype(np.float64), Z.astype(np.float64)
-    opts = ap.ap_opts_default(block=p.block, tol=1e-6, stop=ap.AP_STOP_MAX_REL, min_epochs=1, max_epochs=50000)
+    tol = 1e-4
+    opts = ap.ap_opts_default(block=p.block, tol=tol, stop=ap.AP_STOP_MAX_REL, min_epochs=1, max_epochs=50000)
     ctx = ap.ap_create(_t(p.X), ap.Hyper(p.kernel, p.lengthscale, p.outputscale, p.noise, p.mean), opts)
     st, g, info = ap.ap_mll_grad(ctx, _t(p.y), l, _t(Z))
     assert st == ap.AP_OK, info
@@ -49,7 +50,7 @@ def test_mll_grad_n4096_matern32_31_probes_against_oracle():
     # every column certified by the oracle's FP64 residual
     R = oracle.residual_rows(h, X64, B64, W)
     rel = np.linalg.norm(R, axis=0) / np.linalg.norm(B64, axis=0)
-    assert rel.max() <= 1.05e-6, rel
+    assert rel.max() <= 1.05 * tol, rel
     d = p.d
     alpha = np.array([-0.5] + [0.5 / l] * l)
     V = np.concatenate([W[:, :1], Z64], axis=1)
@@ -78,5 +79,7 @@ def test_mll_grad_n4096_matern32_31_probes_against_oracle():
     print(f"|gpu - estimator| / bound max {np.max(np.abs(g - ref) / bound):.3f}; "
           f"|estimator - exact| / |exact| = {np.linalg.norm(ref - exact) / np.linalg.norm(exact):.3e}; "
           f"epochs {info['epochs']}")
-    assert info["data_fit"] == pytest.approx(0.5 * float(B64[:, 0] @ Wstar[:, 0]), rel=1e-4)
+    # data fit 1/2 y^T u: off by at most 1/2 |y|^T |E_0| (+ FP32 rounding of u)
+    fit = 0.5 * float(B64[:, 0] @ Wstar[:, 0])
+    assert abs(info["data_fit"] - fit) <= 0.5 * float(np.abs(B64[:, 0]) @ (E[:, 0] + 2.0 ** -23 * np.abs(W[:, 0])))
     ap.ap_destroy(ctx)

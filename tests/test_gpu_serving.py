@@ -120,8 +120,11 @@ def test_every_request_meets_its_tolerance_against_the_oracle():
     bound its certified residual implies of the oracle's exact posterior mean
     (Sec. 2): mu_gpu - mu* = s k(x*, X) K_hat^{-1} r, so
     |mu_gpu,t - mu*_t| <= ||s k(x*_t, X)||_2 ||r||_2 / sigma^2 + the FP32 product
-    error of the mean; ||r|| <= (rel_res + e_rec) ||y - mu|| with e_rec the FP32
-    recompute's product error 2e-5 || K_hat |w*| + |y - mu| || / ||y - mu||."""
+    error of the mean; ||r|| <= (rel_res + e_rec) ||y - mu|| with e_rec the error
+    of the recompute that certified rel_res: 2e-5 || K_hat |w*| + |y - mu| || /
+    ||y - mu|| for the plain FP32 one, 2^-23 + 1e-9 || K_hat |w*| + |y - mu| || /
+    ||y - mu|| for the compensated one (the tolerances of the residual parity
+    tests)."""
     import oracle
     reqs = _oracle_requests()
     srv = ap.ApServer(hbm_budget=40 * GB, slots=3)
@@ -136,13 +139,14 @@ def test_every_request_meets_its_tolerance_against_the_oracle():
         mu = oracle.predict_mean(h, X64, w, Xt.astype(np.float64))
         Ks = oracle.gram(h, Xt.astype(np.float64), X64, noise=False)
         Kw = -oracle.residual_rows(h, X64, np.zeros_like(b), np.abs(w))[:, 0]
-        e_rec = 2e-5 * np.linalg.norm(Kw + np.abs(b)) / np.linalg.norm(b)
+        mag = np.linalg.norm(Kw + np.abs(b)) / np.linalg.norm(b)
+        e_rec = 2.0 ** -23 + 1e-9 * mag if res["compensated"] else 2e-5 * mag
         r_norm = (res["rel_res"] + e_rec) * np.linalg.norm(b)
         bound = np.linalg.norm(Ks, axis=1) * r_norm / req.noise + 2e-5 * (np.abs(Ks) @ np.abs(w) + 0.1)
         got = srv.mean(rid).astype(np.float64)
         assert np.all(np.abs(got - mu) <= bound), (req.n, np.max(np.abs(got - mu) / bound))
         print(f"request n={req.n} d={req.d} tol={req.tol:g} prec={prec}: epochs {res['epochs']}, "
-              f"max |mu - mu*| / bound {np.max(np.abs(got - mu) / bound):.3f}")
+              f"compensated {res['compensated']}, max |mu - mu*| / bound {np.max(np.abs(got - mu) / bound):.3f}")
     srv.close()
 
 
