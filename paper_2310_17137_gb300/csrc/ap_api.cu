@@ -703,6 +703,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
 
     double rel[AP_MAX_RHS] = {}, rel_true[AP_MAX_RHS] = {};
     bool have_true = false;
+    int true_epoch = -1;  // epoch at which rel_true was last recomputed
     int epoch = 0, refinements = 0;
     int64_t steps = 0;
     double t_refine = 0.0;
@@ -768,6 +769,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
             ++ctx->divergences;
             met = rel_from(rel);
             have_true = true;
+            true_epoch = epoch;
             for (int k = 0; k < c; ++k) rel_true[k] = rel[k];
             true_prev = rule_measure(ctx->o.stop, c, rel, bn);
         }
@@ -798,6 +800,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
             const bool tracked_met = met;
             met = rel_from(rel_true);
             have_true = true;
+            true_epoch = epoch;
             // The tracked rule held but the plain FP32 recompute does not confirm
             // it: when K_hat |W| is much larger than B the FP32 sums' own error can
             // exceed tol, so AP_RESID_AUTO certifies with the compensated recompute
@@ -833,7 +836,7 @@ ap_status solve_impl(ap_ctx* ctx, const float* B_dev, int c, const float* W0_dev
     // residual of the W it returns: one more FP32 recompute (max_steps runs,
     // used to replay individual steps, are left untouched).
     if (low_precision && status == AP_ERR_NOT_CONVERGED && ctx->o.max_steps <= 0 && epoch > 0 &&
-        !(have_true && (epoch % std::max(1, ctx->o.refine_every)) == 0)) {
+        true_epoch != epoch) {
         AP_CK(cudaEventRecord(ctx->ev_r0, ctx->st));
         AP_TRY(launch_full_residual(ctx, ctx->Bp, ctx->W, ctx->R, kEpiColNorms));
         AP_CK(cudaEventRecord(ctx->ev_r1, ctx->st));

@@ -25,7 +25,6 @@ namespace {
 constexpr int T = kTile;
 constexpr int TP = kTile + 1;
 constexpr int kSolveThreads = 256;
-constexpr int kSolveCtasPerSm = 5;  // register cap of both passes; the tile split fills one wave
 
 __device__ __forceinline__ int64_t packed_tile(int i, int k) { return (int64_t)i * (i + 1) / 2 + k; }
 
@@ -144,7 +143,7 @@ __device__ __forceinline__ void flush_row(const SolveParams& p, int row, int slo
 
 // pass 1: Z_i = sum_{k <= i} X_ik R_I[k]  (X = L^{-1}), tiles in row-major order
 template <int C>
-__global__ void __launch_bounds__(kSolveThreads, kSolveCtasPerSm) solve_lower_kernel(const SolveParams p) {
+__global__ void __launch_bounds__(kSolveThreads) solve_lower_kernel(const SolveParams p) {
     using Tl = SolveTile<C>;
     constexpr int CP = Tl::CP, NQ = Tl::NQ, QPT = (NQ + 3) / 4;
     __shared__ float sx[T * TP];
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kSolveThreads, kSolveCtasPerSm) solve_lower_ke
 // pass 2: Delta_k = sum_{i >= k} X_ik^T Z_i, then W_I += Delta; tiles in
 // column-major order
 template <int C>
-__global__ void __launch_bounds__(kSolveThreads, kSolveCtasPerSm) solve_upper_kernel(const SolveParams p) {
+__global__ void __launch_bounds__(kSolveThreads) solve_upper_kernel(const SolveParams p) {
     using Tl = SolveTile<C>;
     constexpr int CP = Tl::CP, NQ = Tl::NQ, QPT = (NQ + 3) / 4;
     __shared__ float sx[T * TP];
@@ -294,8 +293,7 @@ cudaError_t launch_solve_inst(const SolveParams& p, cudaStream_t st) {
 }  // namespace
 
 void block_solve_layout(int nt, int num_sms, int* tpc, int* maxj) {
-    // as many CTAs as fit at once (one wave), each with an equal share of tiles
-    const int64_t target = (int64_t)kSolveCtasPerSm * std::max(1, num_sms);
+    const int64_t target = 8LL * std::max(1, num_sms);
     *tpc = (int)std::max<int64_t>(1, (solve_ntri(nt) + target - 1) / target);
     *maxj = (nt + *tpc - 1) / *tpc + 1;
 }

@@ -50,14 +50,17 @@ constexpr int kRows = 128;
 constexpr int kChunk = 128;  // columns of the block per chunk
 constexpr int kStages = 4;
 constexpr int kBufs = 3;     // S/P tensor-memory buffers
-constexpr int kXformWarps = 16;
-constexpr int kColsPerWarp = kChunk / (kXformWarps / 4);  // 32 columns of a chunk per warp
-constexpr int kUnits = kColsPerWarp / 16;                  // 16-column work units per warp and chunk
-constexpr int kGroups = kXformWarps / 4;                   // column groups of a chunk (4 warps each)
+constexpr int kColsPerWarp = 32;                   // columns of a chunk per work item (two 16-column units)
+constexpr int kUnits = kColsPerWarp / 16;          // 16-column units per work item
+constexpr int kGroups = kChunk / kColsPerWarp;     // work items (column groups) of a chunk per lane quarter
+constexpr int kSlots = 5;                          // transform warps per lane quarter
+constexpr int kXformWarps = 4 * kSlots;
 constexpr int kLoadWarp = kXformWarps;       // distance MMAs (also owns the tensor memory)
 constexpr int kMmaWarp = kXformWarps + 1;    // contraction MMAs
 constexpr int kCopyWarp = kXformWarps + 2;   // bulk copies of the operand stages
 constexpr int kThreads = (kXformWarps + 3) * 32;
+static_assert(2 * kGroups >= kSlots, "a transform warp has a work item in one of any two consecutive chunks");
+constexpr int kEpiSets = 4;  // named barriers / shared buffers of tile epilogues in flight
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = kBufs * kChunk;  // three accumulators (hi*hi, hi*lo, lo*hi), C columns each
 static_assert(kColAcc + 3 * 32 <= kTmemCols, "tensor memory budget");
@@ -159,6 +162,159 @@ struct TcParams {
     EpiParams epi;         // tiles of 128 rows aligned to blocks (tiles_per_seg = ceil(b / 128))
 };
 
+// What a tile epilogue needs from the kernel: parameters by value and the
+// CTA's shared barriers and buffers.
+struct TcEpiArgs {
+    float* R;
+    const float* Delta;
+    float* scr;
+    int* tick;
+    int* err;
+    long long wait_cycles;
+    float s, noise;
+    int64_t n, col0, ncols;
+    int64_t seg, tiles_per_seg;
+    int flags;
+    double* part_norm;
+    double* part_col;
+    uint64_t* bar_acc_full;  // [kEpiSets]
+    uint64_t* bar_acc_free;
+    volatile int* abort_flag;
+    int* fin;           // [kEpiSets]
+    double* red;        // [kEpiSets][4]
+    double* colred;     // [kEpiSets][4][C]
+    uint32_t tmem_acc;  // first accumulator column (lane 0)
+};
+
+// Epilogue of one row tile (segment sg of this CTA), run by four warps, one per
+// lane quarter, one row per thread.  A whole tile updates R from the
+// accumulators; a tile shared with a neighbouring CTA first stores its part
+// (part 0: chunks from the tile's start, part 1: the rest) in the boundary
+// slot, and the second CTA to arrive updates R from part 0 + part 1, in that
+// order whichever arrives last.  Every path passes the same named barriers so
+// that a failed wait cannot strand the others.  Out of line: it runs once per
+// tile and its registers stay out of the transform loop.  Returns ok.
+template <int C>
+__device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, int sg, int64_t tile, bool whole,
+                                              int part, bool ok) {
+    using namespace tc;
+    const int lane = threadIdx.x & 31;
+    const int es = sg % kEpiSets;
+    const int bar_id = 1 + es;
+    const bool elead = quarter == 0 && lane == 0;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    // segment sg completes phase sg / kEpiSets of its set's barrier
+    if (ok)
+        ok = __all_sync(0xffffffffu, mbar_wait(a.bar_acc_full + es, (uint32_t)((sg / kEpiSets) & 1), a.abort_flag,
+                                              a.err, a.wait_cycles));
+    if (ok) tc_fence_after();
+    const int64_t segi = tile / a.tiles_per_seg;
+    const int64_t seg_lo = segi * a.seg;
+    const int64_t seg_hi = min(seg_lo + a.seg, a.n);
+    const int row = quarter * 32 + lane;
+    const int64_t i = seg_lo + (tile % a.tiles_per_seg) * kRows + row;
+    const bool diag = i >= a.col0 && i < a.col0 + a.ncols;
+    // the three partial products (hi*hi, hi*lo, lo*hi) of 16 columns
+    auto acc16 = [&](int c0, float (&a16)[16]) {
+        uint32_t r[16];
+        tmem_ld16(a.tmem_acc + lane_base + c0, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a16[k] = __uint_as_float(r[k]);
+        tmem_ld16(a.tmem_acc + lane_base + C + c0, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+        tmem_ld16(a.tmem_acc + lane_base + 2 * C + c0, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
+    };
+    bool apply = whole;
+    const int64_t bnd = part == 0 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - 1;
+    float* scr0 = a.scr + ((bnd * 2 + 0) * kRows + row) * C;
+    float* scr1 = a.scr + ((bnd * 2 + 1) * kRows + row) * C;
+    if (!whole) {
+        if (ok) {
+            float* mine = part == 0 ? scr0 : scr1;
+#pragma unroll 1
+            for (int c0 = 0; c0 < C; c0 += 16) {
+                float a16[16];
+                acc16(c0, a16);
+#pragma unroll
+                for (int k = 0; k < 16; k += 4)
+                    __stcg(reinterpret_cast<float4*>(mine + c0 + k), make_float4(a16[k], a16[k + 1], a16[k + 2], a16[k + 3]));
+            }
+            tc_fence_before();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(a.bar_acc_free);
+        __threadfence();
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        if (elead) {
+            int fin = 0;
+            if (ok) {
+                fin = atomicAdd(&a.tick[bnd], 1) == 1;
+                if (fin) a.tick[bnd] = 0;  // both parts are in: ready for the next launch
+                __threadfence();
+            }
+            a.fin[es] = fin;
+        }
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        apply = a.fin[es] != 0;
+    }
+    const bool live = ok && apply && i < seg_hi;
+    // squares are summed in FP32 within a thread and a warp (at most 32 terms
+    // each, relative error below 2e-6) and in FP64 beyond: FP64 arithmetic is
+    // scarce on this part
+    float sqf = 0.0f;
+    double* colred = a.colred + (size_t)es * 4 * C;
+    // 16 columns at a time: the accumulated product, R update, norms
+#pragma unroll 1
+    for (int c0 = 0; c0 < C; c0 += 16) {
+        float a16[16];
+        if (ok && whole) {
+            acc16(c0, a16);
+        } else if (live) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a16[k] = __ldcg(scr0 + c0 + k) + __ldcg(scr1 + c0 + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float v = 0.0f;
+            if (live) {
+                const int c = c0 + k;
+                v = fmaf(-a.s, a16[k], a.R[i * C + c]);
+                if (diag) v = fmaf(-a.noise, a.Delta[(i - a.col0) * C + c], v);
+                a.R[i * C + c] = v;
+                sqf = fmaf(v, v, sqf);
+            }
+            if (apply && (a.flags & kEpiColNorms)) {
+                float w = v * v;
+                for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
+                if (lane == 0) colred[quarter * C + c0 + k] = (double)w;
+            }
+        }
+    }
+    if (whole) {
+        if (ok) tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(a.bar_acc_free);
+    }
+    double sq = sqf;
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+    if (lane == 0) a.red[es * 4 + quarter] = sq;
+    asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+    if (elead && apply) {
+        const double* rd = a.red + es * 4;
+        a.part_norm[tile] = rd[0] + rd[1] + rd[2] + rd[3];
+        if (a.flags & kEpiColNorms)
+            for (int c = 0; c < C; ++c) a.part_col[tile * C + c] = colred[c] + colred[C + c] + colred[2 * C + c] + colred[3 * C + c];
+    }
+    asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+    return ok;
+}
+
 template <int KERN, int C>
 __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams p) {
     using namespace tc;
@@ -179,14 +335,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     // per S/P buffer: S written (distance MMAs), P of one column group written
     // (its four transform warps), P consumed (contraction MMAs)
     __shared__ __align__(8) uint64_t bar_s_full[kBufs], bar_p_full[kBufs][kGroups], bar_buf_free[kBufs];
-    __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_free;
+    // accumulators of a tile complete (one barrier per epilogue set: the tile
+    // epilogues of consecutive segments run on different warps, and a segment
+    // may be a single chunk, so a warp group can reach its wait before the
+    // previous segment's product has completed) / read by the epilogue
+    __shared__ __align__(8) uint64_t bar_acc_full[kEpiSets], bar_acc_free;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ double red_d[32];
     __shared__ int red_i[32];
-    __shared__ double s_colred[4][C];
+    // tile epilogues: consecutive tiles may overlap in time (different warps),
+    // so each takes its own set of reduction buffers and named barrier
+    __shared__ double e_red[kEpiSets][4];
+    __shared__ double s_colred[kEpiSets][4][C];
     __shared__ int s_last;
-    __shared__ int s_fin;  // this CTA completes a shared tile
+    __shared__ int s_fin[kEpiSets];  // this CTA completes a shared tile
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -221,7 +384,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             for (int gq = 0; gq < kGroups; ++gq) mbar_init(&bar_p_full[i][gq], 4);
             mbar_init(&bar_buf_free[i], 1);
         }
-        mbar_init(&bar_acc_full, 1);
+        for (int i = 0; i < kEpiSets; ++i) mbar_init(&bar_acc_full[i], 1);
         mbar_init(&bar_acc_free, 4);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -345,153 +508,86 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 if (!ok) break;
                 tc_commit(&bar_buf_free[buf]);
                 tc_commit(&bar_stage_empty[s]);
-                if (g == total - 1 || q == nq - 1) tc_commit(&bar_acc_full);
+                if (g == total - 1 || q == nq - 1) tc_commit(&bar_acc_full[sg % kEpiSets]);
                 if (++q == nq) q = 0;
             }
         }
     } else {
         // ------------------------------------------------ transform warps
-        // Per chunk a warp takes its 32 columns as two 16-column units (16 entries
-        // per thread each): both tensor-memory loads are in flight together and the
-        // two units are transformed interleaved (the other warps of the scheduler
-        // cover the load latency).
-        const int quarter = warp & 3, group = warp >> 2;
+        // A chunk is 4 work items of 32 columns per lane quarter; the 5
+        // transform warps of a quarter (warp = 4 slot + quarter, which fixes its
+        // TMEM lanes) take the items of the CTA's chunk sequence round-robin (item
+        // 4 c + g to slot (4 c + g) mod 5), each item as two 16-column units (16
+        // entries per thread each) loaded together and transformed interleaved.
+        // Every warp has an item in one of any two consecutive chunks, so no S/P
+        // buffer can run two phases ahead of it.  The tile epilogue of segment sg
+        // runs on the four warps of slot sg mod 5, after they finished their items
+        // up to the segment's last chunk.
+        const int quarter = warp & 3, slot = warp >> 2;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         bool ok = total > 0;
-        // columns of unit (chunk c, unit h of this warp): S there is replaced by [P_hi | P_lo]
-        auto u_addr = [&](int c, int h) -> uint32_t {
-            return tmem + lane_base + (uint32_t)(kChunk * (c % kBufs) + kColsPerWarp * group + 16 * h);
-        };
-        // Segment epilogue (warps 0-3, one row per thread).  A whole tile updates R
-        // from the accumulators; a tile shared with a neighbouring CTA first
-        // stores its part (part 0: chunks from the tile's start, part 1: the rest)
-        // in the boundary slot, and the second CTA to arrive updates R from
-        // part 0 + part 1, in that order whichever arrives last.  Every path passes
-        // the same named barriers so that a failed wait cannot strand the others.
-        auto epilogue = [&](int sg, int64_t tile, bool whole, int part) {
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&bar_acc_full, (uint32_t)(sg & 1), &s_abort, p.err, p.wait_cycles));
-            if (ok) tc_fence_after();
-            const int64_t segi = tile / e.tiles_per_seg;
-            const int64_t seg_lo = segi * e.seg;
-            const int64_t seg_hi = min(seg_lo + e.seg, p.n);
-            const int row = quarter * 32 + lane;
-            const int64_t i = seg_lo + (tile % e.tiles_per_seg) * kRows + row;
-            const bool diag = i >= col0 && i < col0 + ncols;
-            // the three partial products (hi*hi, hi*lo, lo*hi) of 16 columns
-            auto acc16 = [&](int c0, float (&a16)[16]) {
-                uint32_t r[16];
-                tmem_ld16(tmem + lane_base + kColAcc + c0, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int k = 0; k < 16; ++k) a16[k] = __uint_as_float(r[k]);
-                tmem_ld16(tmem + lane_base + kColAcc + C + c0, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
-                tmem_ld16(tmem + lane_base + kColAcc + 2 * C + c0, r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int k = 0; k < 16; ++k) a16[k] += __uint_as_float(r[k]);
-            };
-            bool apply = whole;
-            const int64_t bnd = part == 0 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - 1;
-            float* scr0 = p.scr + ((bnd * 2 + 0) * kRows + row) * C;
-            float* scr1 = p.scr + ((bnd * 2 + 1) * kRows + row) * C;
-            if (!whole) {
-                if (ok) {
-                    float* mine = part == 0 ? scr0 : scr1;
-#pragma unroll 1
-                    for (int c0 = 0; c0 < C; c0 += 16) {
-                        float a16[16];
-                        acc16(c0, a16);
-#pragma unroll
-                        for (int k = 0; k < 16; k += 4)
-                            __stcg(reinterpret_cast<float4*>(mine + c0 + k),
-                                   make_float4(a16[k], a16[k + 1], a16[k + 2], a16[k + 3]));
-                    }
-                    tc_fence_before();
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_acc_free);
-                __threadfence();
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (tid == 0) {
-                    int fin = 0;
-                    if (ok) {
-                        fin = atomicAdd(&p.tick[bnd], 1) == 1;
-                        if (fin) p.tick[bnd] = 0;  // both parts are in: ready for the next launch
-                        __threadfence();
-                    }
-                    s_fin = fin;
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                apply = s_fin != 0;
-            }
-            const bool live = ok && apply && i < seg_hi;
-            // squares are summed in FP32 within a thread and a warp (at most 32 terms
-            // each, relative error below 2e-6) and in FP64 beyond: FP64 arithmetic is
-            // scarce on this part
-            float sqf = 0.0f;
-            // 16 columns at a time: the accumulated product, R update, norms
-#pragma unroll 1
-            for (int c0 = 0; c0 < C; c0 += 16) {
-                float a16[16];
-                if (ok && whole) {
-                    acc16(c0, a16);
-                } else if (live) {
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) a16[k] = __ldcg(scr0 + c0 + k) + __ldcg(scr1 + c0 + k);
-                }
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    float v = 0.0f;
-                    if (live) {
-                        const int c = c0 + k;
-                        v = fmaf(-p.s, a16[k], p.R[i * C + c]);
-                        if (diag) v = fmaf(-p.noise, p.Delta[(i - col0) * C + c], v);
-                        p.R[i * C + c] = v;
-                        sqf = fmaf(v, v, sqf);
-                    }
-                    if (apply && (e.flags & kEpiColNorms)) {
-                        float w = v * v;
-                        for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
-                        if (lane == 0) s_colred[warp][c0 + k] = (double)w;
-                    }
-                }
-            }
-            if (whole) {
-                if (ok) tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_acc_free);
-            }
-            double sq = sqf;
-            for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
-            if (lane == 0) red_d[warp] = sq;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (tid == 0 && apply) {
-                e.part_norm[tile] = red_d[0] + red_d[1] + red_d[2] + red_d[3];
-                if (e.flags & kEpiColNorms)
-                    for (int c = 0; c < C; ++c)
-                        e.part_col[tile * C + c] = s_colred[0][c] + s_colred[1][c] + s_colred[2][c] + s_colred[3][c];
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-        };
-        // per-CTA counters fit in 32 bits (fewer registers in the hot loop)
-        int tile = (int)(u0 / (nq > 0 ? nq : 1)), sg = 0;
-        int q = nq > 0 ? (int)(u0 % nq) : 0, q_first = q;
+        TcEpiArgs ea;
+        ea.R = p.R;
+        ea.Delta = p.Delta;
+        ea.scr = p.scr;
+        ea.tick = p.tick;
+        ea.err = p.err;
+        ea.wait_cycles = p.wait_cycles;
+        ea.s = p.s;
+        ea.noise = p.noise;
+        ea.n = p.n;
+        ea.col0 = col0;
+        ea.ncols = ncols;
+        ea.seg = e.seg;
+        ea.tiles_per_seg = e.tiles_per_seg;
+        ea.flags = e.flags;
+        ea.part_norm = e.part_norm;
+        ea.part_col = e.part_col;
+        ea.bar_acc_full = bar_acc_full;
+        ea.bar_acc_free = &bar_acc_free;
+        ea.abort_flag = &s_abort;
+        ea.fin = s_fin;
+        ea.red = &e_red[0][0];
+        ea.colred = &s_colred[0][0][0];
+        ea.tmem_acc = tmem + kColAcc;
+        // Chunk c of this CTA is pair u0 + c: tile (u0 + c) / nq, chunk (u0 + c) % nq
+        // of the block.  Segment sg = the chunks of tile tile0 + sg.
         const int ntot = (int)total;
-        static_assert(kUnits == 2, "two units per warp and chunk");
-        // one chunk: both 16-column units loaded together, transformed together,
-        // stored in place; then signal the contraction MMA
-        for (int c = 0; c < ntot; ++c) {
+        const int64_t tile0 = nq > 0 ? u0 / nq : 0;
+        const int nseg = ntot > 0 ? (int)((u1 - 1) / nq - tile0 + 1) : 0;
+        auto seg_last = [&](int sg) -> int {  // last chunk of segment sg
+            return (int)min((int64_t)ntot - 1, (tile0 + sg + 1) * nq - 1 - u0);
+        };
+        auto run_epilogue = [&](int sg) {
+            const int c_first = (int)max((int64_t)0, (tile0 + sg) * nq - u0);
+            const int q_first = (int)((u0 + c_first) % nq), q_last = (int)((u0 + seg_last(sg)) % nq);
+            ok = tc_tile_epilogue<C>(ea, quarter, sg, tile0 + sg, q_first == 0 && q_last == nq - 1, q_first == 0 ? 0 : 1,
+                                     ok);
+        };
+        int sg_next = 0, sg_end = nseg > 0 ? seg_last(0) : -1;
+        int c_waited = -1;
+        static_assert(kUnits == 2, "two units per work item");
+        for (int it = slot; it < ntot * kGroups; it += kSlots) {
+            const int c = it / kGroups, group = it % kGroups;
+            // epilogues of the segments that ended before this chunk
+            while (sg_next < nseg && c > sg_end) {
+                if (sg_next % kSlots == slot) run_epilogue(sg_next);
+                if (++sg_next < nseg) sg_end = seg_last(sg_next);
+            }
+            const int buf = c % kBufs;
+            if (c != c_waited) {
+                if (ok)
+                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[buf], (uint32_t)((c / kBufs) & 1), &s_abort,
+                                                          p.err, p.wait_cycles));
+                if (ok) tc_fence_after();
+                c_waited = c;
+            }
+            // columns of unit h of the item: S there is replaced by [P_hi | P_lo]
+            const uint32_t addr0 = tmem + lane_base + (uint32_t)(kChunk * buf + kColsPerWarp * group);
             uint32_t ta[16], tb[16];
-            if (ok)
-                ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[c % kBufs], (uint32_t)((c / kBufs) & 1),
-                                                      &s_abort, p.err, p.wait_cycles));
             if (ok) {
-                tc_fence_after();
-                tmem_ld16(u_addr(c, 0), ta);
-                tmem_ld16(u_addr(c, 1), tb);
+                tmem_ld16(addr0, ta);
+                tmem_ld16(addr0 + 16, tb);
                 tmem_wait_ld();
             }
             uint32_t pa[16], pb[16];  // [P_hi words | P_lo words] of each unit
@@ -508,23 +604,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 pb[8 + k] = pack_bf16(lw.x, lw.y);
             }
             if (ok) {
-                tmem_st16(u_addr(c, 0), pa);
-                tmem_st16(u_addr(c, 1), pb);
+                tmem_st16(addr0, pa);
+                tmem_st16(addr0 + 16, pb);
                 tmem_wait_st();
                 tc_fence_before();
             }
             __syncwarp();
-            if (ok && lane == 0) mbar_arrive(&bar_p_full[c % kBufs][group]);
-            if (c == ntot - 1 || q == nq - 1) {
-                const bool whole = q_first == 0 && q == nq - 1;
-                if (warp < 4) epilogue(sg, tile, whole, q_first == 0 ? 0 : 1);
-            }
-            if (++q == nq) {
-                q = 0;
-                q_first = 0;
-                ++tile;
-                ++sg;
-            }
+            if (ok && lane == 0) mbar_arrive(&bar_p_full[buf][group]);
+        }
+        while (sg_next < nseg) {
+            if (sg_next % kSlots == slot) run_epilogue(sg_next);
+            ++sg_next;
         }
     }
     // ---------------------------------------------------------- teardown

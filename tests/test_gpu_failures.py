@@ -138,5 +138,6 @@ def test_low_precision_divergence_is_rolled_back():
     assert info["diverged"] >= 1 and info["fp32_epochs"] >= 1
     assert np.all(np.isfinite(W.cpu().numpy()))
     # after the roll-back the run is the FP32 form's: no worse than FP32 alone
-    # over the same epochs (up to the noise of their different starting points)
-    assert info["rel_res_true"][0] <= max(1.0 + 1e-6, 1.5 * info32["rel_res_true"][0])
+    # over the same epochs (up to the difference of their starting points), and
+    # its reported residual is that of the W it returns (a recompute at the end)
+    assert info["rel_res_true"][0] <= 1.5 * info32["rel_res_true"][0]
