@@ -551,34 +551,38 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         ea.colred = &s_colred[0][0][0];
         ea.tmem_acc = tmem + kColAcc;
         // Chunk c of this CTA is pair u0 + c: tile (u0 + c) / nq, chunk (u0 + c) % nq
-        // of the block.  Segment sg = the chunks of tile tile0 + sg.
+        // of the block.  Segment sg = the chunks of tile tile0 + sg.  Per-item
+        // bookkeeping is kept in incremental 32-bit counters (no divisions in the
+        // loop): the item's chunk c and group, S/P buffer c mod 3 and its phase.
         const int ntot = (int)total;
         const int64_t tile0 = nq > 0 ? u0 / nq : 0;
         const int nseg = ntot > 0 ? (int)((u1 - 1) / nq - tile0 + 1) : 0;
+        const int qa = nq > 0 ? (int)(u0 % nq) : 0;  // chunk index of the CTA's first pair within its tile
         auto seg_last = [&](int sg) -> int {  // last chunk of segment sg
-            return (int)min((int64_t)ntot - 1, (tile0 + sg + 1) * nq - 1 - u0);
+            return min(ntot - 1, (sg + 1) * nq - 1 - qa);
         };
         auto run_epilogue = [&](int sg) {
-            const int c_first = (int)max((int64_t)0, (tile0 + sg) * nq - u0);
-            const int q_first = (int)((u0 + c_first) % nq), q_last = (int)((u0 + seg_last(sg)) % nq);
+            const int c_first = max(0, sg * nq - qa);
+            const int q_first = (qa + c_first) % nq, q_last = (qa + seg_last(sg)) % nq;
             ok = tc_tile_epilogue<C>(ea, quarter, sg, tile0 + sg, q_first == 0 && q_last == nq - 1, q_first == 0 ? 0 : 1,
                                      ok);
         };
         int sg_next = 0, sg_end = nseg > 0 ? seg_last(0) : -1;
         int c_waited = -1;
         static_assert(kUnits == 2, "two units per work item");
-        for (int it = slot; it < ntot * kGroups; it += kSlots) {
-            const int c = it / kGroups, group = it % kGroups;
+        static_assert(kSlots < 2 * kGroups, "an item advances at most two chunks");
+        int c = slot / kGroups, group = slot % kGroups;
+        int buf = c % kBufs;
+        uint32_t phase = (uint32_t)((c / kBufs) & 1);
+        while (c < ntot) {
             // epilogues of the segments that ended before this chunk
             while (sg_next < nseg && c > sg_end) {
                 if (sg_next % kSlots == slot) run_epilogue(sg_next);
                 if (++sg_next < nseg) sg_end = seg_last(sg_next);
             }
-            const int buf = c % kBufs;
             if (c != c_waited) {
                 if (ok)
-                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[buf], (uint32_t)((c / kBufs) & 1), &s_abort,
-                                                          p.err, p.wait_cycles));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_s_full[buf], phase, &s_abort, p.err, p.wait_cycles));
                 if (ok) tc_fence_after();
                 c_waited = c;
             }
@@ -611,6 +615,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
             }
             __syncwarp();
             if (ok && lane == 0) mbar_arrive(&bar_p_full[buf][group]);
+            // next item: kSlots groups further
+            group += kSlots;
+            while (group >= kGroups) {
+                group -= kGroups;
+                ++c;
+                if (++buf == kBufs) {
+                    buf = 0;
+                    phase ^= 1u;
+                }
+            }
         }
         while (sg_next < nseg) {
             if (sg_next % kSlots == slot) run_epilogue(sg_next);

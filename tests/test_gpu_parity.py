@@ -282,3 +282,18 @@ def test_tensor_core_cache_matches_fp64_cache(n, d, b, kern, ell):
         ap.ap_destroy(ctx)
     scale = np.abs(Ws[1]).max()
     assert np.abs(Ws[0] - Ws[1]).max() <= 4e-4 * scale, np.abs(Ws[0] - Ws[1]).max() / scale
+
+
+@pytest.mark.parametrize("prec", [ap.AP_FP32, ap.AP_BF16_REFINE], ids=["fp32", "bf16"])
+def test_solve_host_equals_device_solve(prec):
+    # the one-shot host-buffer entry point runs the same deterministic solve as
+    # ap_create + ap_solve on device copies of the same inputs
+    p = wl.random_problem(3000, 6, 512, 4, wl.MATERN52, 0.05, 47)
+    opts = dict(block=p.block, precision=prec, tol=1e-4, stop=ap.AP_STOP_MAX_REL, min_epochs=1, max_epochs=200,
+                refine_every=4)
+    st_h, W_h, info_h = ap.ap_solve_host(p.X, p.B, _hyper(p), ap.ap_opts_default(**opts))
+    ctx = _ctx(p, **{k: v for k, v in opts.items() if k != "block"})
+    st_d, W_d, info_d, _ = ap.ap_solve(ctx, _t(p.B))
+    assert st_h == st_d and info_h["epochs"] == info_d["epochs"]
+    np.testing.assert_array_equal(W_h, W_d.cpu().numpy())
+    ap.ap_destroy(ctx)
