@@ -256,7 +256,7 @@ def run_ours(args, rank: int, world: int):
             c1.record(stream)
             torch.cuda.synchronize()
             cms = c0.elapsed_time(c1) / csteps
-            cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / args.steps
+            cent = sum(float(p.n) * float(p.block) + i["kernel_entries"] for i in cinfos) / csteps
             compare[name] = {"ms_per_step": cms, "kernel_entries_per_s": cent / (cms * 1e-3),
                              "update_kernel_ms": cinfos[-1]["t_update_s"] / max(1, cinfos[-1]["n_update"]) * 1e3,
                              "solve_s": statistics.median(i["t_solve_s"] for i in cinfos),
