@@ -309,6 +309,24 @@ int64_t ap_launch_count(const ap_ctx* ctx);
  * Cholesky cache, work buffers); 0 for NULL. */
 size_t ap_device_bytes(const ap_ctx* ctx);
 
+/* Bounds-checked build only (the library built with AP_CHECKED defined, a
+ * separate file from the product library; no counterpart in the paper).
+ * Every kernel of that build checks its tile and row indices against the sizes
+ * it was given before the accesses they guard; a failing check skips the
+ * access and records its source line.  This call synchronises the current
+ * device, reads and clears the records of every translation unit, writes
+ * "unit:line" of the first one found into where[0..cap) (NUL-terminated, may
+ * be NULL) and returns how many units recorded a failure (0: none).  The
+ * product build returns -1 and touches nothing. */
+int32_t ap_bounds_violations(char* where, int32_t cap);
+
+/* Bounds-checked build only: a one-thread kernel reads element `index` of an
+ * 8-element device buffer through the same check, so that an index outside
+ * [0, 8) is recorded (and the read skipped) as a failed check; shows that the
+ * recording works.  AP_OK, AP_ERR_NOMEM, AP_ERR_CUDA; AP_ERR_UNSUPPORTED in
+ * the product build. */
+ap_status ap_bounds_selftest(int32_t index);
+
 /* Measured SFU throughput of the current device, in results per SM clock, of
  * the two operations kernel evaluation is made of: ex2.approx (every kernel)
  * and sqrt.approx (Matern kernels).  No counterpart in the paper; the

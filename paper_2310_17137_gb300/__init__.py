@@ -28,7 +28,7 @@ from ._capi import (AP_ERR_SCRATCH_LIMIT, AP_ERR_CANCELLED, AP_BF16_REFINE, AP_E
 
 __all__ = ["ApError", "Hyper", "Context", "ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve",
            "ap_residual", "ap_predict_mean", "ap_grad_quadforms", "ap_mll_grad", "ap_destroy",
-           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ap_tracked_residual", "ap_device_bytes", "ap_solve_host", "ApServer",
+           "ap_status_str", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval", "ap_grad_quadforms_static", "ap_tracked_residual", "ap_device_bytes", "ap_solve_host", "ap_bounds_violations", "ap_bounds_selftest", "ApServer",
            "MLLDataFit"]
 
 
@@ -244,6 +244,21 @@ def ap_mll_grad(ctx: Context, y, n_probes: int, Z=None):
 
 def ap_launch_count(ctx: Context) -> int:
     return int(_capi.load().ap_launch_count(ctx.handle))
+
+
+def ap_bounds_violations():
+    """(count, "unit:line" of the first) of failed index checks since the last
+    call, in the bounds-checked build (AP_CHECKED=1); (-1, "") in the product
+    build.  Synchronises the device."""
+    buf = ctypes.create_string_buffer(256)
+    n = int(_capi.load().ap_bounds_violations(buf, 256))
+    return n, buf.value.decode()
+
+
+def ap_bounds_selftest(index: int) -> int:
+    """Status of a one-thread read of element `index` of an 8-element buffer
+    through the index check (recorded when out of range, checked build only)."""
+    return int(_capi.load().ap_bounds_selftest(int(index)))
 
 
 def ap_device_bytes(ctx: Context) -> int:

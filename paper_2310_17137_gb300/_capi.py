@@ -28,7 +28,8 @@ EXPORTS = ["ap_opts_default", "ap_create", "ap_set_hyper", "ap_solve", "ap_resid
            "ap_sizeof_opts", "ap_sizeof_info", "ap_sizeof_hyper", "ap_launch_count", "ap_sfu_rates", "ap_phi_fp64_eval",
            "ap_grad_quadforms_static", "ap_server_create", "ap_server_submit", "ap_server_poll",
            "ap_server_wait", "ap_server_destroy", "ap_sizeof_request", "ap_sizeof_request_result",
-           "ap_tracked_residual", "ap_device_bytes", "ap_last_cuda_error", "ap_server_cancel", "ap_solve_host"]
+           "ap_tracked_residual", "ap_device_bytes", "ap_last_cuda_error", "ap_server_cancel", "ap_solve_host",
+           "ap_bounds_violations", "ap_bounds_selftest"]
 
 
 class ap_hyper(ctypes.Structure):
@@ -79,21 +80,29 @@ class ap_request_result(ctypes.Structure):
 _lib = None
 
 
+def checked() -> bool:
+    """True when this process uses the bounds-checked build (environment
+    variable AP_CHECKED=1, read once at the first load)."""
+    return os.environ.get("AP_CHECKED", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libap.so (building it first if it is missing).  There is no fallback:
-    if the CUDA library cannot be built or loaded this raises."""
+    """Load libap.so, or libap_checked.so under AP_CHECKED=1 (building it first
+    if it is missing).  There is no fallback: if the CUDA library cannot be
+    built or loaded this raises."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
+    path = lib_path()
+    if not os.path.exists(path):
         if not build_if_missing:
-            raise ImportError(f"{_build.LIB} is missing; run __graft_entry__.build()")
-        _build.build()
-    L = ctypes.CDLL(_build.LIB)
+            raise ImportError(f"{path} is missing; run __graft_entry__.build()")
+        _build.build(checked=checked())
+    L = ctypes.CDLL(path)
     P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     st = ctypes.c_int
     sig = {
@@ -112,6 +121,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "ap_launch_count": (i64, [P]),
         "ap_device_bytes": (ctypes.c_size_t, [P]),
         "ap_last_cuda_error": (i32, [P]),
+        "ap_bounds_violations": (i32, [ctypes.c_char_p, i32]),
+        "ap_bounds_selftest": (st, [i32]),
         "ap_tracked_residual": (st, [P, i32, P]),
         "ap_sfu_rates": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "ap_phi_fp64_eval": (st, [i32, P, i64, P]),

@@ -3,6 +3,12 @@
 Each translation unit compiles to an object under ``_build/`` in parallel, then
 nvcc links the shared library next to this file.  Objects are rebuilt when
 their source or any header is newer.  No CMake, no torch extension machinery.
+
+``build(checked=True)`` makes the bounds-checked variant instead: the same
+sources compiled with AP_CHECKED defined (every kernel checks its tile and row
+indices before the accesses they guard, see ap_bounds_violations in ap.h),
+objects under ``_build_checked/`` and the library ``libap_checked.so``.  It is
+a diagnostic build for tests; the product is libap.so.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libap.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libap_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -41,15 +49,16 @@ def _stale(obj: str, src: str, newest_header: float) -> bool:
     return t < os.path.getmtime(src) or t < newest_header
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra: list | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, extra: list | None = None, checked: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     newest = max(os.path.getmtime(h) for h in _headers())
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DAP_CHECKED"] if checked else [])
 
     def compile_one(src: str):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         if not _stale(obj, src, newest):
             return obj, None
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
@@ -70,14 +79,14 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list | None = N
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     objs = [o for o, _ in results]
-    if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -6,6 +6,7 @@
 // graph and replayed; the host reads only the c column norms at the end of an
 // epoch to apply the stopping rule of Sec. 5.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -912,9 +913,48 @@ void grad_finish(const GradView& v, const double* raw, double* out_host) {
     out_host[v.d + 1] = raw[v.D + 1];
 }
 
+#ifdef AP_CHECKED
+namespace {
+struct ChkUnit {
+    const char* unit;
+    unsigned int (*read_and_clear)();
+};
+std::vector<ChkUnit>& chk_units() {
+    static std::vector<ChkUnit> units;
+    return units;
+}
+}  // namespace
+
+int chk_register(const char* unit, unsigned int (*read_and_clear)()) {
+    chk_units().push_back({unit, read_and_clear});
+    return 1;
+}
+#endif
+
 }  // namespace ap
 
 extern "C" {
+
+int32_t ap_bounds_violations(char* where, int32_t cap) {
+#ifdef AP_CHECKED
+    cudaDeviceSynchronize();
+    int32_t count = 0;
+    for (const ap::ChkUnit& u : ap::chk_units()) {
+        const unsigned int line = u.read_and_clear();
+        if (!line) continue;
+        if (count == 0 && where && cap > 0) {
+            const char* base = strrchr(u.unit, '/');
+            snprintf(where, (size_t)cap, "%s:%u", base ? base + 1 : u.unit, line);
+        }
+        ++count;
+    }
+    return count;
+#else
+    (void)where;
+    (void)cap;
+    return -1;
+#endif
+}
 
 void ap_opts_default(ap_opts* o) {
     if (!o) return;

@@ -9,6 +9,32 @@
 
 namespace ap {
 
+// Bounds-checked build (compiled with -DAP_CHECKED into a separate library):
+// AP_CHK(cond) guards an index before the access it protects.  A failing check
+// records its source line in a device word of its translation unit (the first
+// one wins) and yields false, so that the caller skips the access instead of
+// faulting; ap_bounds_violations reads and clears the words of every unit.  In
+// the product build AP_CHK(cond) is `true` and compiles away.
+#ifdef AP_CHECKED
+namespace {
+__device__ unsigned int g_chk_line;  // one per translation unit
+}
+#define AP_CHK(cond) ((cond) ? true : (atomicCAS(&g_chk_line, 0u, (unsigned int)__LINE__), false))
+// Host registry of the per-unit words (defined in ap_api.cu).
+int chk_register(const char* unit, unsigned int (*read_and_clear)());
+namespace {
+unsigned int chk_read_and_clear() {
+    unsigned int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_chk_line, sizeof v) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_chk_line, &zero, sizeof zero);
+    return v;
+}
+const int g_chk_registered = chk_register(__BASE_FILE__, &chk_read_and_clear);
+}  // namespace
+#else
+#define AP_CHK(cond) true
+#endif
+
 constexpr int kTile = 64;           // tile edge of the block-Cholesky cache
 constexpr int kKmvThreads = 128;    // threads per CTA of the kernel-matrix products
 constexpr int kKmvTN = 64;          // columns staged per shared-memory chunk

@@ -99,10 +99,11 @@ __device__ __forceinline__ void flush_row(const SolveParams& p, int row, int slo
                                           const float (&acc)[QPT][4], int r, int g, int* s_last, F&& emit) {
     constexpr int NQ = CP / 4;
     float* dst = p.spart + ((int64_t)row * p.maxj + slot) * T * CP;
+    const bool slot_ok = AP_CHK(slot >= 0 && slot < p.maxj && nslots <= p.maxj && row < p.nt);
 #pragma unroll
     for (int u = 0; u < QPT; ++u) {
         const int quad = g + 4 * u;
-        if (quad < NQ)
+        if (quad < NQ && slot_ok)
             *reinterpret_cast<float4*>(dst + r * CP + 4 * quad) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
     }
     __threadfence();
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_lower_kernel(const SolveP
     const int tid = threadIdx.x;
     const int I = *p.sel;
     const int64_t lo = (int64_t)I * p.b;
+    if (!AP_CHK(I >= 0 && lo < p.n)) return;
     const int64_t bI = min(p.b, p.n - lo);
     const int64_t ntri = solve_ntri(p.nt);
     const float* Lb = p.Linv + (int64_t)I * ntri * T * T;
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_upper_kernel(const SolveP
     const int I = *p.sel;
     const int nt = p.nt;
     const int64_t lo = (int64_t)I * p.b;
+    if (!AP_CHK(I >= 0 && lo < p.n)) return;
     const int64_t bI = min(p.b, p.n - lo);
     const int64_t ntri = solve_ntri(nt);
     const float* Lb = p.Linv + (int64_t)I * ntri * T * T;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_upper_kernel(const SolveP
                                    if (c >= C) return;
                                    const int64_t li = (int64_t)kk * T + qq;
                                    if (li < p.b) p.Delta[li * C + c] = li < bI ? sum : 0.0f;
-                                   if (li < bI) p.W[(lo + li) * C + c] += sum;
+                                   if (li < bI && AP_CHK(lo + li < p.n)) p.W[(lo + li) * C + c] += sum;
                                });
 #pragma unroll
             for (int uu = 0; uu < QPT; ++uu) acc[uu][0] = acc[uu][1] = acc[uu][2] = acc[uu][3] = 0.0f;

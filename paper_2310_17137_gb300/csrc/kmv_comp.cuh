@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
     const int64_t c_hi = min(col0 + ncols, c_lo + cs);
 
     const int64_t i = r0 + tid;
-    const bool live = i < r1;
+    const bool live = i < r1 && AP_CHK(i < p.na);
     float xh[D], xl[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -79,11 +79,13 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
     for (int64_t cb = c_lo; cb < c_hi; cb += kKmvTN) {
         const int cnt = (int)min((int64_t)kKmvTN, c_hi - cb);
         __syncthreads();
-        for (int t = tid; t < cnt * D; t += kKmvThreads) {
-            s_xh[t] = p.Xb[cb * D + t];
-            s_xl[t] = p.Xb_lo[cb * D + t];
+        if (AP_CHK(cb >= 0 && cb + cnt <= p.nb) && AP_CHK(cb - col0 >= 0 && cb - col0 + cnt <= ncols)) {
+            for (int t = tid; t < cnt * D; t += kKmvThreads) {
+                s_xh[t] = p.Xb[cb * D + t];
+                s_xl[t] = p.Xb_lo[cb * D + t];
+            }
+            for (int t = tid; t < cnt * C; t += kKmvThreads) s_v[t] = p.V[(cb - col0) * C + t];
         }
-        for (int t = tid; t < cnt * C; t += kKmvThreads) s_v[t] = p.V[(cb - col0) * C + t];
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             df::F2 t2 = {0.0f, 0.0f};
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         df::F2 v = df::mul_f(acc[c], p.s);
-        if (diag) v = df::add(v, df::two_prod(p.noise, p.V[(i - col0) * C + c]));
+        if (diag && AP_CHK(i - col0 >= 0 && i - col0 < ncols)) v = df::add(v, df::two_prod(p.noise, p.V[(i - col0) * C + c]));
         s_ph[tid * C + c] = v.h;
         s_pl[tid * C + c] = v.l;
     }
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
                 sum = df::add(sum, df::F2{cluster.map_shared_rank(s_ph, src)[lr * C + c],
                                           cluster.map_shared_rank(s_pl, src)[lr * C + c]});
         }
-        if (ii < r1) {
+        if (ii < r1 && AP_CHK(ii < p.na)) {
             const float bv = p.base ? p.base[ii * C + c] : p.base_const;
             const df::F2 o2 = df::add_f(df::F2{p.sgn * sum.h, p.sgn * sum.l}, bv);
             const float o = o2.h + o2.l;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
     }
     if (e.flags & kEpiBlockNorms) {
         double tot = cta_sum_d(sq, red_d);
-        if (tid == 0) e.part_norm[tile * S + rank] = tot;
+        if (tid == 0 && AP_CHK(tile * S + rank < e.ntiles * e.S)) e.part_norm[tile * S + rank] = tot;
     }
     if (e.flags & kEpiColNorms) {
         __syncthreads();
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kKmvThreads) kmv_comp_kernel(const KmvParams p
         if (tid < C) {
             double a = 0.0;
             for (int k = tid; k < kKmvThreads; k += C) a += s_col[k];
-            e.part_col[(tile * S + rank) * C + tid] = a;
+            if (AP_CHK(tile * S + rank < e.ntiles * e.S)) e.part_col[(tile * S + rank) * C + tid] = a;
         }
     }
     if (S > 1) cg::this_cluster().sync();

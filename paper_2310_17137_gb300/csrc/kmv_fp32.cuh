@@ -91,7 +91,7 @@ __device__ void epi_finalize(const EpiParams& e, double* red_d, int* red_i) {
         for (int J = tid; J < e.m; J += nth) {
             double acc = 0.0;
             const double* src = e.part_norm + (int64_t)J * per;
-            for (int64_t t = 0; t < per; ++t) acc += __ldcg(src + t);
+            for (int64_t t = 0; t < per && AP_CHK((int64_t)J * per + t < e.ntiles * e.S); ++t) acc += __ldcg(src + t);
             e.norms_out[J] = acc;
             if (!isfinite(acc)) bad = 1;
             if (acc > best) { best = acc; bi = J; }
@@ -157,7 +157,7 @@ __device__ __forceinline__ void epi_store(const KmvParams& p, float* s_part, int
                 sum += peer[lr * C + c];
             }
         }
-        if (i < r1) {
+        if (i < r1 && AP_CHK(i < p.na)) {
             const float bv = p.base ? p.base[i * C + c] : p.base_const;
             const float o = fmaf(p.sgn, sum, bv);
             p.out[i * C + c] = o;
@@ -169,7 +169,7 @@ __device__ __forceinline__ void epi_store(const KmvParams& p, float* s_part, int
     const EpiParams& e = p.epi;
     if (e.flags & kEpiBlockNorms) {
         double tot = cta_sum_d(sq, red_d);
-        if (tid == 0) e.part_norm[part_idx] = tot;
+        if (tid == 0 && AP_CHK(part_idx < e.ntiles * e.S)) e.part_norm[part_idx] = tot;
     }
     if (e.flags & kEpiColNorms) {
         __syncthreads();
@@ -178,7 +178,7 @@ __device__ __forceinline__ void epi_store(const KmvParams& p, float* s_part, int
         if (tid < C) {
             double acc = 0.0;
             for (int k = tid; k < kKmvThreads; k += C) acc += s_col[k];
-            e.part_col[part_idx * C + tid] = acc;
+            if (AP_CHK(part_idx < e.ntiles * e.S)) e.part_col[part_idx * C + tid] = acc;
         }
     }
 }
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kKmvThreads, 4) kmv_fp32_kernel(const KmvParam
 #pragma unroll
         for (int k4 = 0; k4 < D / 4; ++k4) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < r1) v = reinterpret_cast<const float4*>(p.Xa + i * D)[k4];
+            if (i < r1 && AP_CHK(i < p.na)) v = reinterpret_cast<const float4*>(p.Xa + i * D)[k4];
             xa[q][4 * k4 + 0] = v.x;
             xa[q][4 * k4 + 1] = v.y;
             xa[q][4 * k4 + 2] = v.z;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kKmvThreads, 4) kmv_fp32_kernel(const KmvParam
         for (int64_t cb = c_lo; cb < c_hi; cb += kKmvTN) {
             const int cnt = (int)min((int64_t)kKmvTN, c_hi - cb);
             __syncthreads();
-            {
+            if (AP_CHK(cb >= 0 && cb + cnt <= p.nb) && AP_CHK(cb - col0 >= 0 && cb - col0 + cnt <= ncols)) {
                 const float4* gx = reinterpret_cast<const float4*>(p.Xb + cb * D);
                 float4* sx = reinterpret_cast<float4*>(s_xb);
                 for (int t = tid; t < cnt * D / 4; t += kKmvThreads) sx[t] = __ldg(gx + t);
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kKmvThreads, 4) kmv_fp32_kernel(const KmvParam
     for (int64_t cb = c_lo; cb < c_hi; cb += kKmvTN) {
         const int cnt = (int)min((int64_t)kKmvTN, c_hi - cb);
         __syncthreads();
-        {
+        if (AP_CHK(cb >= 0 && cb + cnt <= p.nb) && AP_CHK(cb - col0 >= 0 && cb - col0 + cnt <= ncols)) {
             const float4* gx = reinterpret_cast<const float4*>(p.Xb + cb * D);
             float4* sx = reinterpret_cast<float4*>(s_xb);
             for (int t = tid; t < cnt * D / 4; t += kKmvThreads) sx[t] = __ldg(gx + t);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kKmvThreads, 4) kmv_fp32_kernel(const KmvParam
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             float v = p.s * acc[q][c];
-            if (diag) v = fmaf(p.noise, __ldg(p.V + (i - col0) * C + c), v);
+            if (diag && AP_CHK(i - col0 >= 0 && i - col0 < ncols)) v = fmaf(p.noise, __ldg(p.V + (i - col0) * C + c), v);
             s_part[lr * C + c] = v;
         }
     }
@@ -428,14 +428,14 @@ __global__ void __launch_bounds__(kKmvThreads) norms_select_kernel(const float* 
     const int64_t r0 = seg_lo + (tile % e.tiles_per_seg) * tile_rows;
     const int64_t r1 = min(r0 + tile_rows, seg_hi);
     double sq = 0.0, colacc = 0.0;
-    for (int64_t t = tid; t < (r1 - r0) * C; t += kKmvThreads) {
+    for (int64_t t = tid; t < (r1 - r0) * C && AP_CHK(r1 <= n); t += kKmvThreads) {
         const double v = (double)R[r0 * C + t];
         sq += v * v;
         colacc += v * v;
     }
     if (e.flags & kEpiBlockNorms) {
         double tot = cta_sum_d(sq, red_d);
-        if (tid == 0) e.part_norm[tile] = tot;
+        if (tid == 0 && AP_CHK(tile < e.ntiles)) e.part_norm[tile] = tot;
     }
     if (e.flags & kEpiColNorms) {
         __syncthreads();
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kKmvThreads) norms_select_kernel(const float* 
         if (tid < C) {
             double acc = 0.0;
             for (int k = tid; k < kKmvThreads; k += C) acc += s_col[k];
-            e.part_col[tile * C + tid] = acc;
+            if (AP_CHK(tile < e.ntiles)) e.part_col[tile * C + tid] = acc;
         }
     }
     epi_ticket<C>(e, red_d, red_i, &s_last);

@@ -8,7 +8,7 @@
 //      value split into an FP16 hi/lo pair; the three cross products of the
 //      pairs are laid out along K, so K = 3d + 4 rounded up to 16 and d <= 4
 //      needs a single MMA), FP32 accumulation in tensor memory;
-//   2. sixteen transform warps load t from tensor memory, evaluate phi on the
+//   2. twenty transform warps load t from tensor memory, evaluate phi on the
 //      SFU and write P = phi back as a BF16 hi/lo pair, in place: every 16
 //      FP32 columns of S become 8 columns of P_hi followed by 8 of P_lo;
 //   3. acc += P Delta^T on the tensor cores with P read from tensor memory and
@@ -18,18 +18,22 @@
 // R_i -= s acc_i + sigma^2 Delta_i (index diagonal), with the block norms of the
 // new R written per tile for the ticketed last-CTA selection.
 //
-// Warp roles: warps 0-15 transform (warp w owns TMEM lanes 32 (w % 4).. and
-// columns 32 (w / 4).. of a chunk, in two halves of 16; four transform warps per
-// scheduler hide the SFU and tensor-memory latencies); warp 16 lane 0 issues
-// the distance MMAs, warp 17 lane 0 the contraction MMAs and warp 18 lane 0 the
-// bulk copies, so that no issuer waits behind another one's barriers.  The
-// hi*hi and hi*lo products of the contraction are one MMA of width 2C (Delta_hi
-// and Delta_lo stacked), lo*hi a second one into its own accumulator; the three
-// partial sums are added in the epilogue.  S/P live in a
-// ring of three tensor-memory buffers (a buffer is reused once the contraction
-// that read its P has completed), operands in a ring of shared-memory stages;
-// everything is synchronised by mbarriers, and every wait is bounded in time
-// and reports a timeout through the error flag instead of hanging.
+// Warp roles: warps 0-19 transform (warp w owns TMEM lanes 32 (w % 4).. and
+// takes 32-column work items of the chunks round-robin with the other four
+// warps of its lane quarter; five transform warps per scheduler hide the SFU
+// and tensor-memory latencies); warp 20 issues the distance MMAs, warp 21 the
+// contraction MMAs and warp 22 (lane 0) the bulk copies, so that no issuer
+// waits behind another one's barriers.  The MMA issuers run their loops on the
+// whole warp, with warp-uniform addresses and descriptors, and issue from one
+// elected lane: a loop in a single lane of a diverged warp paid some 70-80
+// cycles per MMA and made the contraction issuer the bottleneck.  The hi*hi
+// and hi*lo products of the contraction are one MMA of width 2C (Delta_hi and
+// Delta_lo stacked), lo*hi a second one into its own accumulator; the three
+// partial sums are added in the epilogue.  S/P live in a ring of three
+// tensor-memory buffers (a buffer is reused once the contraction that read its
+// P has completed), operands in a ring of shared-memory stages; everything is
+// synchronised by mbarriers, and every wait is bounded in time and reports a
+// timeout through the error flag instead of hanging.
 //
 // Work split: the (tile, chunk) pairs of a step, in tile-major order, are cut
 // into one equal contiguous range per persistent CTA (instead of whole tiles,
@@ -174,6 +178,7 @@ struct TcEpiArgs {
     float s, noise;
     int64_t n, col0, ncols;
     int64_t seg, tiles_per_seg;
+    int64_t ntiles;  // row tiles of the step (size of part_norm)
     int flags;
     double* part_norm;
     double* part_col;
@@ -237,13 +242,16 @@ __device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, in
     if (!whole) {
         if (ok) {
             float* mine = part == 0 ? scr0 : scr1;
+            if (!AP_CHK(bnd >= 0 && bnd < (int64_t)gridDim.x)) mine = nullptr;
 #pragma unroll 1
             for (int c0 = 0; c0 < C; c0 += 16) {
                 float a16[16];
                 acc16(c0, a16);
 #pragma unroll
                 for (int k = 0; k < 16; k += 4)
-                    __stcg(reinterpret_cast<float4*>(mine + c0 + k), make_float4(a16[k], a16[k + 1], a16[k + 2], a16[k + 3]));
+                    if (mine)
+                        __stcg(reinterpret_cast<float4*>(mine + c0 + k),
+                               make_float4(a16[k], a16[k + 1], a16[k + 2], a16[k + 3]));
             }
             tc_fence_before();
         }
@@ -254,7 +262,7 @@ __device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, in
         if (elead) {
             int fin = 0;
             if (ok) {
-                fin = atomicAdd(&a.tick[bnd], 1) == 1;
+                fin = AP_CHK(bnd >= 0 && bnd < (int64_t)gridDim.x) && atomicAdd(&a.tick[bnd], 1) == 1;
                 if (fin) a.tick[bnd] = 0;  // both parts are in: ready for the next launch
                 __threadfence();
             }
@@ -263,7 +271,8 @@ __device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, in
         asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
         apply = a.fin[es] != 0;
     }
-    const bool live = ok && apply && i < seg_hi;
+    const bool live = ok && apply && i < seg_hi && AP_CHK(i < a.n) &&
+                      (whole || AP_CHK(bnd >= 0 && bnd < (int64_t)gridDim.x));
     // squares are summed in FP32 within a thread and a warp (at most 32 terms
     // each, relative error below 2e-6) and in FP64 beyond: FP64 arithmetic is
     // scarce on this part
@@ -285,7 +294,7 @@ __device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, in
             if (live) {
                 const int c = c0 + k;
                 v = fmaf(-a.s, a16[k], a.R[i * C + c]);
-                if (diag) v = fmaf(-a.noise, a.Delta[(i - a.col0) * C + c], v);
+                if (diag && AP_CHK(i - a.col0 < a.ncols)) v = fmaf(-a.noise, a.Delta[(i - a.col0) * C + c], v);
                 a.R[i * C + c] = v;
                 sqf = fmaf(v, v, sqf);
             }
@@ -305,7 +314,7 @@ __device__ __noinline__ bool tc_tile_epilogue(const TcEpiArgs a, int quarter, in
     for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
     if (lane == 0) a.red[es * 4 + quarter] = sq;
     asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-    if (elead && apply) {
+    if (elead && apply && AP_CHK(tile >= 0 && tile < a.ntiles)) {
         const double* rd = a.red + es * 4;
         a.part_norm[tile] = rd[0] + rd[1] + rd[2] + rd[3];
         if (a.flags & kEpiColNorms)
@@ -403,12 +412,22 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
     if (warp == kCopyWarp) {
         // ------------------------------------------------ bulk-copy issuer
         if (lane == 0 && total > 0) {
+            // a bound shorter than the default (tests of the timeout path) is
+            // enforced here with non-blocking probes: the copy issuer runs ahead
+            // of the pipeline, so its waits are the ones that run out
+            const bool strict = p.wait_cycles < kWaitCycles;
+            auto copy_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+                return strict ? mbar_wait_strict(bar, parity, &s_abort, p.err, p.wait_cycles)
+                              : mbar_wait(bar, parity, &s_abort, p.err, p.wait_cycles);
+            };
             auto issue_xa = [&](int64_t sg, int64_t tile) -> bool {
                 const int xb = (int)(sg & 1);
                 const int64_t u = sg >> 1;
-                if (u >= 1 && !mbar_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1), &s_abort, p.err, p.wait_cycles)) return false;
-                mbar_expect_tx(&bar_xa_full[xb], kXaBytes);
-                bulk_g2s(s_xa + (size_t)xb * kXaBytes, p.XA + (size_t)tile * kXaBytes, kXaBytes, &bar_xa_full[xb]);
+                if (u >= 1 && !copy_wait(&bar_xa_empty[xb], (uint32_t)((u - 1) & 1))) return false;
+                // (an index that fails its check arrives with no bytes: nothing is copied)
+                const bool in = AP_CHK(tile >= 0 && tile < e.ntiles);
+                mbar_expect_tx(&bar_xa_full[xb], in ? kXaBytes : 0u);
+                if (in) bulk_g2s(s_xa + (size_t)xb * kXaBytes, p.XA + (size_t)tile * kXaBytes, kXaBytes, &bar_xa_full[xb]);
                 return true;
             };
             int64_t tile = u0 / nq, sg = 0;
@@ -419,12 +438,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 if ((i == 0 || q == 0) && tile < last_tile) ok = issue_xa(sg + 1, tile + 1);
                 const int s = (int)(i % kStages);
                 const int64_t u = i / kStages;
-                if (ok && u >= 1) ok = mbar_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1), &s_abort, p.err, p.wait_cycles);
+                if (ok && u >= 1) ok = copy_wait(&bar_stage_empty[s], (uint32_t)((u - 1) & 1));
                 if (!ok) break;
                 uint8_t* dst = s_stage + (size_t)s * kStageBytes;
-                mbar_expect_tx(&bar_stage_full[s], kStageBytes);
-                bulk_g2s(dst, p.XB + ((size_t)I * p.cpb + q) * kXbBytes, kXbBytes, &bar_stage_full[s]);
-                bulk_g2s(dst + kXbBytes, p.DT + (size_t)q * kDtBytes, kDtBytes, &bar_stage_full[s]);
+                const bool in = AP_CHK(I >= 0 && I < e.m && q >= 0 && q < p.cpb);
+                mbar_expect_tx(&bar_stage_full[s], in ? kStageBytes : 0u);
+                if (in) {
+                    bulk_g2s(dst, p.XB + ((size_t)I * p.cpb + q) * kXbBytes, kXbBytes, &bar_stage_full[s]);
+                    bulk_g2s(dst + kXbBytes, p.DT + (size_t)q * kDtBytes, kDtBytes, &bar_stage_full[s]);
+                }
                 if (++q == nq) {
                     q = 0;
                     ++tile;
@@ -434,45 +456,58 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         }
     } else if (warp == kLoadWarp) {
         // ------------------------------------------------ distance MMA issuer
-        if (lane == 0 && total > 0) {
+        // The whole warp runs the loop (warp-uniform addresses and descriptors);
+        // one elected lane issues the MMAs and their commits.
+        if (total > 0) {
             constexpr uint32_t idesc_d = instr_desc(0, kRows, kChunk);  // F16 x F16 -> F32, 128 x 128
+            const bool leader = elect_one();
             bool ok = true;
             int64_t sg = -1;
             int q = (int)(u0 % nq), xb = 0;
-            uint32_t xa = 0;
+            uint64_t da = 0;
+            const uint64_t db0 = smem_desc(smem_u32(s_stage), 128, kSboX);
             for (int64_t g = 0; g < total && ok; ++g) {
                 if (g == 0 || q == 0) {
                     ++sg;
                     xb = (int)(sg & 1);
-                    ok = mbar_wait(&bar_xa_full[xb], (uint32_t)((sg >> 1) & 1), &s_abort, p.err, p.wait_cycles);
-                    xa = smem_u32(s_xa + (size_t)xb * kXaBytes);
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait(&bar_xa_full[xb], (uint32_t)((sg >> 1) & 1), &s_abort, p.err, p.wait_cycles));
+                    da = smem_desc(smem_u32(s_xa + (size_t)xb * kXaBytes), 128, kSboX);
                     if (!ok) break;
                 }
                 const int s = (int)(g % kStages);
                 const int buf = (int)(g % kBufs);
                 const int64_t use = g / kBufs;
-                ok = mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err, p.wait_cycles);
-                if (ok && use >= 1) ok = mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err, p.wait_cycles);
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(&bar_stage_full[s], (uint32_t)((g / kStages) & 1), &s_abort, p.err, p.wait_cycles));
+                if (ok && use >= 1)
+                    ok = __all_sync(0xffffffffu, mbar_wait(&bar_buf_free[buf], (uint32_t)((use - 1) & 1), &s_abort, p.err,
+                                                          p.wait_cycles));
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t xbs = smem_u32(s_stage + (size_t)s * kStageBytes);
+                // descriptor address fields advance by 16-byte units: stage s, K-step ks (256 B)
+                const uint64_t db = db0 + (uint64_t)((s * kStageBytes) >> 4);
                 const uint32_t dS = tmem + (uint32_t)(kChunk * buf);
-                for (int ks = 0; ks < KSTEPS_D; ++ks) {
-                    const uint32_t off = ks * 256;
-                    mma_ss(dS, smem_desc(xa + off, 128, kSboX), smem_desc(xbs + off, 128, kSboX), idesc_d,
-                           ks > 0 ? 1u : 0u);
+                if (leader) {
+                    for (int ks = 0; ks < KSTEPS_D; ++ks)
+                        mma_ss(dS, da + (uint64_t)(ks * 16), db + (uint64_t)(ks * 16), idesc_d, ks > 0 ? 1u : 0u);
+                    tc_commit(&bar_s_full[buf]);
+                    if (g == total - 1 || q == nq - 1) tc_commit(&bar_xa_empty[xb]);
                 }
-                tc_commit(&bar_s_full[buf]);
-                if (g == total - 1 || q == nq - 1) tc_commit(&bar_xa_empty[xb]);
+                __syncwarp();
                 if (++q == nq) q = 0;
             }
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ contraction MMA issuer
-        if (lane == 0 && total > 0) {
+        // (whole warp in the loop, elected lane issuing, as above)
+        if (total > 0) {
             // BF16 x BF16 -> F32: 128 x 2C (P_hi against [Delta_hi; Delta_lo]) and 128 x C
             constexpr uint32_t idesc_c2 = instr_desc(1, kRows, 2 * C);
             constexpr uint32_t idesc_c = instr_desc(1, kRows, C);
+            const bool leader = elect_one();
+            const uint64_t dt0 = smem_desc(smem_u32(s_stage + kXbBytes), 128, kSboD);
+            const uint32_t a01 = tmem + kColAcc, a2 = a01 + 2 * C;
             bool ok = true;
             int64_t sg = -1;
             int q = (int)(u0 % nq);
@@ -480,14 +515,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
                 const bool first = g == 0 || q == 0;
                 const int buf = (int)(g % kBufs);
                 const int s = (int)(g % kStages);
-                if (first && ++sg >= 1) ok = mbar_wait(&bar_acc_free, (uint32_t)((sg - 1) & 1), &s_abort, p.err, p.wait_cycles);
+                const uint32_t ph = (uint32_t)((g / kBufs) & 1);
+                if (first && ++sg >= 1)
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait(&bar_acc_free, (uint32_t)((sg - 1) & 1), &s_abort, p.err, p.wait_cycles));
                 if (!ok) break;
                 // Delta^T of the stage: C rows of Delta_hi, then C rows of Delta_lo
                 // (consecutive 8-row groups), so one N = 2C product gives hi*hi
                 // and hi*lo side by side in accumulator columns [0, 2C)
-                const uint32_t dth = smem_u32(s_stage + (size_t)s * kStageBytes + kXbBytes);
+                const uint64_t dth = dt0 + (uint64_t)((s * kStageBytes) >> 4);
                 const uint32_t pb = tmem + (uint32_t)(kChunk * buf);
-                const uint32_t a01 = tmem + kColAcc, a2 = a01 + 2 * C;
                 // K-step ks: 16 BF16 values of P = 8 columns of P_hi at 16 ks and 8
                 // of P_lo at 16 ks + 8; two 16-byte core columns of Delta^T (core
                 // columns 128 B apart).  The K-steps of a column group start as
@@ -495,20 +532,26 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
 #pragma unroll
                 for (int ks = 0; ks < KSTEPS_C; ++ks) {
                     if (ks % kUnits == 0) {
-                        ok = mbar_wait(&bar_p_full[buf][ks / kUnits], (uint32_t)((g / kBufs) & 1), &s_abort, p.err, p.wait_cycles);
+                        ok = __all_sync(0xffffffffu, mbar_wait(&bar_p_full[buf][ks / kUnits], ph, &s_abort, p.err,
+                                                              p.wait_cycles));
                         if (!ok) break;
                         tc_fence_after();
                     }
                     const uint32_t acc = (first && ks == 0) ? 0u : 1u;
-                    const uint32_t boff = ks * 256;
+                    const uint64_t bd = dth + (uint64_t)(ks * 16);
                     const uint32_t pH = pb + 16u * ks, pL = pH + 8u;
-                    mma_ts(a01, pH, smem_desc(dth + boff, 128, kSboD), idesc_c2, acc);
-                    mma_ts(a2, pL, smem_desc(dth + boff, 128, kSboD), idesc_c, acc);
+                    if (leader) {
+                        mma_ts(a01, pH, bd, idesc_c2, acc);
+                        mma_ts(a2, pL, bd, idesc_c, acc);
+                    }
                 }
                 if (!ok) break;
-                tc_commit(&bar_buf_free[buf]);
-                tc_commit(&bar_stage_empty[s]);
-                if (g == total - 1 || q == nq - 1) tc_commit(&bar_acc_full[sg % kEpiSets]);
+                if (leader) {
+                    tc_commit(&bar_buf_free[buf]);
+                    tc_commit(&bar_stage_empty[s]);
+                    if (g == total - 1 || q == nq - 1) tc_commit(&bar_acc_full[sg % kEpiSets]);
+                }
+                __syncwarp();
                 if (++q == nq) q = 0;
             }
         }
@@ -540,6 +583,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         ea.ncols = ncols;
         ea.seg = e.seg;
         ea.tiles_per_seg = e.tiles_per_seg;
+        ea.ntiles = e.ntiles;
         ea.flags = e.flags;
         ea.part_norm = e.part_norm;
         ea.part_col = e.part_col;

@@ -41,7 +41,7 @@ __global__ void prep_inputs_kernel(const float* __restrict__ X, int64_t n, int d
         const int64_t i = t / D;
         const int k = (int)(t % D);
         float hi = 0.0f, lo = 0.0f;
-        if (k < d) {
+        if (k < d && AP_CHK(i < n)) {
             const float x = X[i * d + k];
             if (!isfinite(x) && bad) *bad = 1;
             hi = x * sh.v[k];
@@ -227,3 +227,33 @@ cudaError_t launch_dot0(const float* W, int C, const float* Y, int cy, int64_t n
 }
 
 }  // namespace ap
+
+// ---------------------------------------------------- bounds-check self-test
+namespace ap {
+namespace {
+
+// One thread reads element `index` of an 8-element buffer through AP_CHK: in
+// the checked build an index outside [0, 8) is recorded and the read skipped.
+__global__ void bounds_selftest_kernel(const float* __restrict__ buf, int index, float* __restrict__ out) {
+    float v = 0.0f;
+    if (AP_CHK(index >= 0 && index < 8)) v = buf[index];
+    *out = v;
+}
+
+}  // namespace
+}  // namespace ap
+
+extern "C" ap_status ap_bounds_selftest(int32_t index) {
+#ifdef AP_CHECKED
+    float* d = nullptr;
+    if (cudaMalloc(&d, 9 * sizeof(float)) != cudaSuccess) return AP_ERR_NOMEM;
+    cudaMemset(d, 0, 9 * sizeof(float));
+    ap::bounds_selftest_kernel<<<1, 1>>>(d, index, d + 8);
+    const cudaError_t err = cudaDeviceSynchronize();
+    cudaFree(d);
+    return err == cudaSuccess ? AP_OK : AP_ERR_CUDA;
+#else
+    (void)index;
+    return AP_ERR_UNSUPPORTED;
+#endif
+}

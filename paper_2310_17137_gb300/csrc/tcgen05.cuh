@@ -45,11 +45,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, ui
     return ok != 0;
 }
 
+// Non-blocking probe of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase.  Gives up when `limit` SM clock cycles
 // have passed or when another thread of the CTA already gave up (abort flag),
 // and reports it.
-// A bound shorter than the default also drops the suspend hint, so that the
-// bound is what ends the wait.
+// A bound shorter than the default also drops the suspend hint (a try_wait
+// can still block for a while in hardware).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* err_flag, long long limit = kWaitCycles) {
     const uint32_t hint = limit >= kWaitCycles ? kSuspendHintNs : 0u;
@@ -57,6 +70,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity, hint)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > limit) {
+            *abort_flag = 1;
+            atomicExch(err_flag, 1);
+            return false;
+        }
+    }
+}
+
+// Wait under a bound shorter than the default that probes with the
+// non-blocking test_wait, so that the bound alone ends it: with a bound of one
+// cycle, any phase not complete at the first probe gives up.  Out of line and
+// used only where the short bound is asked for, off the transform warps' path.
+static __device__ __noinline__ bool mbar_wait_strict(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                     int* err_flag, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (clock64() - t0 > limit) {
             *abort_flag = 1;
@@ -76,6 +107,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One lane of a converged warp (the lowest active one, so the same lane every
+// time): the MMA issuers run their loops on the whole warp, so that addresses
+// and descriptors stay warp-uniform, and issue each MMA and commit from the
+// elected lane.  A commit tracks the MMAs of the thread that issues it.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r));
+    return r != 0;
+}
 
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

@@ -79,3 +79,14 @@ def test_package_has_no_cpu_fallback():
         if fn.endswith(".py"):
             txt = open(os.path.join(src_dir, fn)).read()
             assert "import oracle" not in txt and "from oracle" not in txt, fn
+
+
+def test_product_build_has_no_index_checks(lib):
+    # the bounds checks exist only in the separately built libap_checked.so
+    # (tests/test_gpu_checked.py); the product library answers without a GPU
+    import paper_2310_17137_gb300 as ap
+    from paper_2310_17137_gb300 import _capi
+    if _capi.checked():
+        pytest.skip("this process uses the checked build")
+    assert ap.ap_bounds_violations() == (-1, "")
+    assert ap.ap_bounds_selftest(100) == ap.AP_ERR_UNSUPPORTED

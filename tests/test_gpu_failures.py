@@ -59,10 +59,12 @@ def test_nan_in_inputs_is_reported(bad):
 
 
 def test_wait_that_runs_out_gives_timeout_and_the_device_stays_usable():
-    # a one-cycle bound (and no suspend hint) on every mbarrier wait of the
-    # tensor-core update: the first wait that is not already complete gives up,
-    # the kernel lets its copies and MMAs land, frees its tensor memory and returns
-    p = wl.random_problem(5000, 3, 512, 16, wl.MATERN52, 0.05, 43)
+    # a one-cycle bound on every mbarrier wait of the tensor-core update: the
+    # bulk-copy issuer probes its waits without blocking, and it runs ahead of
+    # the pipeline until it must wait for a shared-memory stage to be consumed
+    # (every CTA here has more chunks than stages), so that wait gives up; the
+    # kernel lets its copies and MMAs land, frees its tensor memory and returns
+    p = wl.random_problem(20000, 3, 1024, 16, wl.MATERN52, 0.05, 43)
     ctx = ap.ap_create(_t(p.X), _hyper(p), ap.ap_opts_default(block=p.block, precision=ap.AP_BF16_REFINE,
                                                               wait_limit_cycles=1, max_epochs=2))
     with pytest.raises(ap.ApError) as e:
