@@ -569,31 +569,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         const int quarter = warp & 3, slot = warp >> 2;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         bool ok = total > 0;
-        TcEpiArgs ea;
-        ea.R = p.R;
-        ea.Delta = p.Delta;
-        ea.scr = p.scr;
-        ea.tick = p.tick;
-        ea.err = p.err;
-        ea.wait_cycles = p.wait_cycles;
-        ea.s = p.s;
-        ea.noise = p.noise;
-        ea.n = p.n;
-        ea.col0 = col0;
-        ea.ncols = ncols;
-        ea.seg = e.seg;
-        ea.tiles_per_seg = e.tiles_per_seg;
-        ea.ntiles = e.ntiles;
-        ea.flags = e.flags;
-        ea.part_norm = e.part_norm;
-        ea.part_col = e.part_col;
-        ea.bar_acc_full = bar_acc_full;
-        ea.bar_acc_free = &bar_acc_free;
-        ea.abort_flag = &s_abort;
-        ea.fin = s_fin;
-        ea.red = &e_red[0][0];
-        ea.colred = &s_colred[0][0][0];
-        ea.tmem_acc = tmem + kColAcc;
         // Chunk c of this CTA is pair u0 + c: tile (u0 + c) / nq, chunk (u0 + c) % nq
         // of the block.  Segment sg = the chunks of tile tile0 + sg.  Per-item
         // bookkeeping is kept in incremental 32-bit counters (no divisions in the
@@ -605,7 +580,35 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
         auto seg_last = [&](int sg) -> int {  // last chunk of segment sg
             return min(ntot - 1, (sg + 1) * nq - 1 - qa);
         };
+        // the epilogue's arguments are assembled at each call (from kernel
+        // parameters and shared addresses), so that none of them stays live
+        // across the transform loop
         auto run_epilogue = [&](int sg) {
+            TcEpiArgs ea;
+            ea.R = p.R;
+            ea.Delta = p.Delta;
+            ea.scr = p.scr;
+            ea.tick = p.tick;
+            ea.err = p.err;
+            ea.wait_cycles = p.wait_cycles;
+            ea.s = p.s;
+            ea.noise = p.noise;
+            ea.n = p.n;
+            ea.col0 = col0;
+            ea.ncols = ncols;
+            ea.seg = e.seg;
+            ea.tiles_per_seg = e.tiles_per_seg;
+            ea.ntiles = e.ntiles;
+            ea.flags = e.flags;
+            ea.part_norm = e.part_norm;
+            ea.part_col = e.part_col;
+            ea.bar_acc_full = bar_acc_full;
+            ea.bar_acc_free = &bar_acc_free;
+            ea.abort_flag = &s_abort;
+            ea.fin = s_fin;
+            ea.red = &e_red[0][0];
+            ea.colred = &s_colred[0][0][0];
+            ea.tmem_acc = tmem + kColAcc;
             const int c_first = max(0, sg * nq - qa);
             const int q_first = (qa + c_first) % nq, q_last = (qa + seg_last(sg)) % nq;
             ok = tc_tile_epilogue<C>(ea, quarter, sg, tile0 + sg, q_first == 0 && q_last == nq - 1, q_first == 0 ? 0 : 1,
