@@ -95,3 +95,57 @@ def test_slice_products_are_exact_and_close_to_the_fp64_product():
         bound = Fraction(2) ** -50 * K * Fraction(max(abs(a))) * Fraction(max(abs(c))) * 8 \
             + Fraction(abs(float(exact))) * Fraction(2) ** -52
         assert abs(got - exact) <= bound, float(abs(got - exact) / bound)
+
+
+def _tc_constants():
+    """The pipeline constants of the tensor-core update, read from its source."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2310_17137_gb300", "csrc", "kmv_tc.cu")).read()
+    vals = {}
+    for name in ("kRows", "kChunk", "kStages", "kBufs", "kColsPerWarp", "kSlots", "kTcMaxKdp"):
+        m = re.search(r"constexpr int %s = (\d+);" % name, src)
+        assert m, name
+        vals[name] = int(m.group(1))
+    vals["kGroups"] = vals["kChunk"] // vals["kColsPerWarp"]
+    return vals
+
+
+def _slot_chunks(slot, n_slots, n_groups, n_chunks):
+    """Chunks of the work items of one transform warp: items c * n_groups + g, taken
+    round-robin by the n_slots warps of a lane quarter starting at their slot."""
+    return [i // n_groups for i in range(slot, n_chunks * n_groups, n_slots)]
+
+
+def _max_gap(n_slots, n_groups, n_chunks=64):
+    gaps = []
+    for s in range(n_slots):
+        ch = _slot_chunks(s, n_slots, n_groups, n_chunks)
+        assert ch[0] < n_groups and all(b >= a for a, b in zip(ch, ch[1:]))
+        gaps += [b - a for a, b in zip(ch, ch[1:])]
+    return max(gaps)
+
+
+def test_transform_schedule_keeps_buffer_phases_unambiguous():
+    # A transform warp waits on the S barrier of its item's buffer by phase parity.
+    # Its previous item's S was complete, and the distance MMAs complete in chunk
+    # order, so the buffer has completed at least the phase of chunk c - kBufs as
+    # long as consecutive items of a warp are at most kBufs chunks apart; it cannot
+    # complete the phase after c before this warp's P of chunk c is consumed.
+    k = _tc_constants()
+    items = sorted(i for s in range(k["kSlots"]) for i in range(s, 64 * k["kGroups"], k["kSlots"]))
+    assert items == list(range(64 * k["kGroups"]))  # every item of a quarter exactly once
+    assert _max_gap(k["kSlots"], k["kGroups"]) <= k["kBufs"]
+    # the rule is not vacuous: thirteen warps per quarter would skip a whole ring
+    assert _max_gap(13, k["kGroups"]) > k["kBufs"]
+
+
+def test_tensor_core_update_fits_tmem_and_shared_memory():
+    k = _tc_constants()
+    for C in (16, 32):
+        assert k["kBufs"] * k["kChunk"] + 3 * C <= 512  # S/P ring + three accumulators
+    kdp, C = k["kTcMaxKdp"], 32
+    xa = k["kRows"] * kdp * 2
+    stage = k["kChunk"] * kdp * 2 + 2 * C * k["kChunk"] * 2
+    assert 2 * xa + k["kStages"] * stage + 1024 <= 227 * 1024 - 8 * 1024  # dynamic + static headroom
