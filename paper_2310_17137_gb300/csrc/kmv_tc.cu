@@ -147,6 +147,25 @@ __device__ __forceinline__ float2 phi_tc2(float t0, float t1) {
 
 }  // namespace tc
 
+// Spinning wait (no suspension: the phase is picked up as soon as it completes),
+// bounded like mbar_wait; the contraction issuer's wait for P in the RBF form.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err_flag,
+                                               long long limit) {
+    if (tc::mbar_test_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; ++it) {
+        if (tc::mbar_test_wait(bar, parity)) return true;
+        if ((it & 31u) == 0) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                *abort_flag = 1;
+                atomicExch(err_flag, 1);
+                return false;
+            }
+        }
+    }
+}
+
 // -------------------------------------------------------------- kernel params
 struct TcParams {
     const uint8_t* XA;     // row operand tiles: ntiles x (128 x kdp fp16)
@@ -532,8 +551,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) kmv_tc_kernel(const TcParams 
 #pragma unroll
                 for (int ks = 0; ks < KSTEPS_C; ++ks) {
                     if (ks % kUnits == 0) {
-                        ok = __all_sync(0xffffffffu, mbar_wait(&bar_p_full[buf][ks / kUnits], ph, &s_abort, p.err,
-                                                              p.wait_cycles));
+                        // RBF (one SFU operation per entry, short chunk periods) picks P
+                        // up by spinning; for the Matern kernels the spin's issue slots
+                        // cost the transform warps of this scheduler more than it saves
+                        uint64_t* pf = &bar_p_full[buf][ks / kUnits];
+                        const bool got = KERN == AP_RBF ? mbar_wait_spin(pf, ph, &s_abort, p.err, p.wait_cycles)
+                                                        : mbar_wait(pf, ph, &s_abort, p.err, p.wait_cycles);
+                        ok = __all_sync(0xffffffffu, got);
                         if (!ok) break;
                         tc_fence_after();
                     }
