@@ -90,3 +90,19 @@ def test_product_build_has_no_index_checks(lib):
         pytest.skip("this process uses the checked build")
     assert ap.ap_bounds_violations() == (-1, "")
     assert ap.ap_bounds_selftest(100) == ap.AP_ERR_UNSUPPORTED
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    # the bounds-checked variant (AP_CHECKED) is a separate library with the same
+    # ABI; it is built here (objects cached under _build_checked/) and loaded next
+    # to the product library without a GPU
+    import shutil
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("nvcc not available")
+    from paper_2310_17137_gb300 import _capi
+    from paper_2310_17137_gb300 import build as _build
+    path = _build.build(checked=True)
+    assert path.endswith("libap_checked.so") and path != _build.LIB
+    L = ctypes.CDLL(path)
+    for name in _capi.EXPORTS:
+        assert hasattr(L, name), name
